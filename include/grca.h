@@ -1,0 +1,220 @@
+/* grca.h — C ABI of the GB300-native GRCA ray caster (libgrca.so).
+ *
+ * GRCA (Gajmer Ray-Casting Algorithm) answers, per frame, the problem of
+ * Sec. 1.1 (Eq. brute): for every ray of every spinning LiDAR, the closest
+ * triangle it intersects and its distance.  It inverts the question — which
+ * rays can each triangle hit — and needs no acceleration structure: each
+ * (triangle, LiDAR) pair is moved into the emitter frame, its elevation and
+ * azimuth extent is bounded against the channel cones/plane (Sec. 3.2-3.7)
+ * and the azimuth grid, optional range culling is applied (App. A.4.1), the
+ * candidate (channel, ray) spans are expanded, each candidate gets a
+ * watertight ray-triangle test and a per-ray closest-hit reduction keeps
+ * (distance, triangle id) (App. A.4.1 Step 5, Sec. A.5.2).
+ *
+ * Conventions (all entry points):
+ *   - Return a grca_status: GRCA_OK (0) or a negative error code; no
+ *     exception crosses the ABI.  grca_status_string() names each code.
+ *   - All device work is asynchronous on the caller's `stream` (a
+ *     cudaStream_t passed as void*; NULL = legacy default stream).  Errors
+ *     raised by device work (queue capacity overflow) are reported by
+ *     grca_get_stats() on that stream.
+ *   - One context per host thread; a context is bound to one CUDA device.
+ *   - World frame: any right-handed frame; sensor axes f (forward), r (right),
+ *     u (up) are orthonormal in it.  Azimuth increases from f toward r
+ *     ("clockwise seen from above", Sec. 3.1), elevation upward from the
+ *     f-r plane.
+ *   - Rays of a cast are laid out sensor-major in `sensor_ids` order, then
+ *     channel (ascending elevation), then ray (ascending azimuth): global ray
+ *     index g = O_n + j * n_rays_n + i (App. A.4.1, Step 5).
+ */
+#ifndef GRCA_H
+#define GRCA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct grca_ctx grca_ctx; /* opaque; created and owned by the library */
+typedef int32_t grca_status;
+
+enum {
+    GRCA_OK = 0,
+    GRCA_ERR_INVALID_ARG = -1, /* null pointer, bad size, bad sensor, unsorted table ... */
+    GRCA_ERR_OOM = -2,         /* device or host allocation failed */
+    GRCA_ERR_CUDA = -3,        /* a CUDA runtime call failed (see grca_last_cuda_error) */
+    GRCA_ERR_CAPACITY = -4,    /* a device work queue overflowed; results of that cast are invalid */
+    GRCA_ERR_TIMEOUT = -5,     /* a bounded device wait gave up */
+    GRCA_ERR_NOT_READY = -6    /* no triangles uploaded, or no sensors */
+};
+
+/* Where a host-API buffer lives. */
+enum { GRCA_MEM_HOST = 0, GRCA_MEM_DEVICE = 1 };
+
+/* grca_cast flags. */
+enum {
+    /* FP32 tests, then FP64 re-tests of every ray flagged by the FP32 pass
+     * (a candidate within the FP32 error bound of an edge, a t whose FP32
+     * error bound is large, or two hits on one ray whose FP32 distances are
+     * within the tie band).  Off: plain FP32 path. */
+    GRCA_CAST_FP64_RECHECK = 1u << 0,
+    /* Keep only triangles facing the sensor: n = (v1-v0)x(v2-v0) with
+     * n.(o - v0) > 0 (reading of App. A.4.1 Step 1, sign fixed to the
+     * usual outward-normal convention). */
+    GRCA_CAST_CULL_BACKFACE = 1u << 1,
+    /* Debug: no culling, every ray against every triangle (small scenes). */
+    GRCA_CAST_BRUTE = 1u << 2,
+    /* Capture the frame's kernel sequence into a CUDA graph and replay it on
+     * later casts with the same shape, flags and buffers. */
+    GRCA_CAST_GRAPH = 1u << 3,
+    /* Debug: append every tested (ray, triangle) candidate to the dump buffer
+     * set by grca_set_debug_dump (for superset checks of the culling). */
+    GRCA_CAST_DUMP_CANDIDATES = 1u << 4
+};
+
+/* Context options (all fields 0 = library default). */
+typedef struct {
+    uint64_t big_pair_capacity;  /* pairs deferred to the per-channel span pass (default 4M, 112 B each) */
+    uint64_t chunk_capacity;     /* test chunks in the work queue (default 32M, 16 B each) */
+    uint64_t recheck_capacity;   /* (ray, triangle) pairs queued for FP64 re-test (default 8M, 8 B each) */
+    uint32_t inline_max;         /* candidates per pair tested inline by the culling pass (default 16) */
+    uint32_t chunk_rays;         /* rays per test chunk (default 64) */
+    uint32_t cull_block;         /* threads per culling block (default 256) */
+    uint32_t cull_blocks_per_sm; /* resident culling blocks per SM (default 4) */
+} grca_options;
+
+/* One spinning LiDAR (Sec. 3.1, Eq. ray_dir and the centred angle grid).
+ *   origin, f, r, u : position and orthonormal axes, FP64, world frame.
+ *   elev_rad        : n_channels elevations in radians, strictly ascending,
+ *                     |elev| < pi/2.  Copied by the library.
+ *   n_rays, theta0, dtheta : azimuth grid theta_i = theta0 + i*dtheta,
+ *                     i in [0, n_rays); n_rays*dtheta <= 2*pi (+1e-9).  When
+ *                     n_rays*dtheta == 2*pi (to 1e-9) the grid closes the
+ *                     circle and spans wrap around it.
+ *   d_min, d_max    : a hit counts only if d_min <= t <= d_max (per-hit
+ *                     reading of the range filter of App. A.4.1); d_max may
+ *                     be +inf.  0 <= d_min <= d_max.
+ * Limits: n_channels <= 1024, n_rays <= 32768, at most 64 sensors per cast. */
+typedef struct {
+    double origin[3];
+    double f[3];
+    double r[3];
+    double u[3];
+    const double* elev_rad;
+    uint32_t n_channels;
+    uint32_t n_rays;
+    double theta0;
+    double dtheta;
+    double d_min;
+    double d_max;
+} grca_sensor_desc;
+
+/* Counters of the last cast (valid after grca_get_stats, which syncs). */
+typedef struct {
+    uint64_t pairs;           /* (triangle, sensor) pairs visited = n_sensors * n_tris */
+    uint64_t pairs_live;      /* pairs whose candidate span is non-empty */
+    uint64_t candidates;      /* (channel, ray) candidates in the pair spans */
+    uint64_t candidates_inline; /* of which tested inline by the culling pass */
+    uint64_t big_pairs;       /* pairs deferred to the per-channel span pass */
+    uint64_t chunks;          /* test chunks emitted by that pass */
+    uint64_t tests;           /* ray-triangle tests run */
+    uint64_t hits;            /* FP32 hits committed to the closest-hit keys */
+    uint64_t uncertain;       /* FP32 tests sent to the FP64 re-test */
+    uint64_t ties;            /* tie events between FP32 hits on one ray */
+    uint64_t flagged_rays;    /* rays resolved by the FP64 re-test */
+    uint64_t recheck_pairs;   /* (ray, triangle) pairs re-tested in FP64 */
+    uint64_t n_rays;          /* rays in the last cast */
+    uint32_t device_error;    /* bit mask of device-side errors (0 = none) */
+    uint32_t reserved;
+} grca_stats;
+
+/* Create a context on CUDA device `device`.  `opt` may be NULL.
+ * *out receives the context (owned by the library; free with grca_destroy). */
+grca_status grca_create(grca_ctx** out, int device, const grca_options* opt);
+
+/* Free every device and host buffer of the context.  NULL is a no-op. */
+void grca_destroy(grca_ctx* ctx);
+
+/* Register a sensor (Sec. 3.1).  The description and its elevation table are
+ * copied.  *out_sensor_id receives a dense id (0, 1, ...). */
+grca_status grca_create_sensor(grca_ctx* ctx, const grca_sensor_desc* desc, int32_t* out_sensor_id);
+
+/* Move a sensor: new origin and orthonormal axes (FP64, world frame). */
+grca_status grca_set_sensor_pose(grca_ctx* ctx, int32_t sensor_id, const double origin[3], const double f[3],
+                                 const double r[3], const double u[3]);
+
+/* (Re)define the scene: n_tris unindexed FP32 triangles, layout [n][3][3]
+ * (triangle, vertex, xyz), world frame.  `where` = GRCA_MEM_HOST or
+ * GRCA_MEM_DEVICE tells where `xyz` lives.  The library copies the data into
+ * a device buffer it owns (asynchronous on `stream`; a host source must stay
+ * valid until the stream reaches the copy).  Triangle ids are 0..n_tris-1. */
+grca_status grca_upload_triangles(grca_ctx* ctx, const float* xyz, uint32_t n_tris, int where, void* stream);
+
+/* Overwrite triangles [first_tri, first_tri + n_tris) with new vertices
+ * (same layout), e.g. the dynamic part of the scene every frame. */
+grca_status grca_update_vertices(grca_ctx* ctx, const float* xyz, uint32_t first_tri, uint32_t n_tris, int where,
+                                 void* stream);
+
+/* Cast one frame for the listed sensors (Sec. 1.1 problem statement).
+ *   out_dist : DEVICE pointer, one float per ray: distance t of the closest
+ *              hit, +inf on a miss (Sec. A.5.1).
+ *   out_tri  : DEVICE pointer, one uint32 per ray: triangle id, 0xFFFFFFFF on
+ *              a miss.  Ties in distance go to the lower id.
+ * Both arrays hold sum over sensors of n_channels*n_rays entries in the
+ * layout above and are owned by the caller.  `flags` = GRCA_CAST_*. */
+grca_status grca_cast(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_sensors, float* out_dist,
+                      uint32_t* out_tri, uint32_t flags, void* stream);
+
+/* Same as grca_cast with HOST output arrays: the frame's vertices
+ * (`xyz_dynamic`, n_dynamic triangles starting at first_dynamic, HOST) are
+ * copied in first, the results copied back into the host arrays, and the
+ * call returns once they are there (end-to-end frame). */
+grca_status grca_cast_host(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_sensors, const float* xyz_dynamic,
+                           uint32_t first_dynamic, uint32_t n_dynamic, float* out_dist_host,
+                           uint32_t* out_tri_host, uint32_t flags, void* stream);
+
+/* Time the launch-parameter candidates (culling block shape, inline
+ * candidate limit, chunk size) on the current scene for these sensors and
+ * flags, and keep the fastest for later casts of the same shape.  Runs casts
+ * into the given output buffers; synchronous.  *out_ms (nullable) receives
+ * the best frame time. */
+grca_status grca_autotune(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_sensors, float* out_dist,
+                          uint32_t* out_tri, uint32_t flags, void* stream, float* out_ms);
+
+/* Debug dump for GRCA_CAST_DUMP_CANDIDATES: a DEVICE buffer of `capacity`
+ * (global ray id, triangle id) uint32 pairs and a DEVICE uint32 counter
+ * (caller zeroes it).  Pass NULLs to detach. */
+grca_status grca_set_debug_dump(grca_ctx* ctx, uint32_t* pairs, uint64_t capacity, uint32_t* counter);
+
+/* Counters and device error bits of the last cast; synchronizes `stream`.
+ * Returns GRCA_ERR_CAPACITY if a work queue overflowed in that cast. */
+grca_status grca_get_stats(grca_ctx* ctx, grca_stats* out, void* stream);
+
+/* Number of kernels the last cast launched (or replayed in its graph). */
+uint32_t grca_last_launch_count(grca_ctx* ctx);
+
+/* Per-kernel timing with CUDA events (tracing aid).  While enabled, casts
+ * are launched without graph replay and each kernel of the frame is
+ * bracketed by two events recorded on the cast's stream.  Enabling or
+ * disabling resets the totals. */
+grca_status grca_profile_enable(grca_ctx* ctx, int enable);
+
+/* Totals since grca_profile_enable: for kernel k < min(max, *n_out) of the
+ * frame sequence (k_init, k_cull, k_expand, k_test, k_recheck_rays,
+ * k_recheck_pairs, k_decode), its name (static string), number of launches and
+ * summed device time in ms.  Synchronizes with the recorded events.
+ * *n_out receives the number of kernel kinds. */
+grca_status grca_profile_read(grca_ctx* ctx, uint32_t max, const char** names, uint64_t* launches,
+                              double* total_ms, uint32_t* n_out);
+
+/* Static description of a status code. */
+const char* grca_status_string(grca_status status);
+
+/* Text of the last CUDA error seen by this context ("" if none). */
+const char* grca_last_cuda_error(grca_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRCA_H */

@@ -1,0 +1,799 @@
+// Host runtime of libgrca.so: the C ABI declared in include/grca.h.
+//
+// Owns the device scene buffer, the sensor tables, the per-ray scratch and
+// the device work queues; builds the per-cast sensor descriptors; launches
+// (or replays as a CUDA graph) the frame's kernel sequence; runs the
+// launch-parameter autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "grca.h"
+#include "grca_internal.h"
+
+using namespace grca;
+
+namespace {
+
+constexpr int RING = 64;  // pinned staging slots for per-cast sensor descriptors
+
+struct SensorHost {
+    grca_sensor_desc d;
+    std::vector<double> elev;
+    bool full;
+};
+
+struct GraphKey {
+    uint32_t n_sensors, n_rays, total_ch, flags, n_tris;
+    const void* out_dist;
+    const void* out_tri;
+    const void* tris;
+    const void* keys;
+    const void* dump;
+    int cull_block, cull_bps, inline_max, chunk_rays;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(n_sensors, n_rays, total_ch, flags, n_tris, out_dist, out_tri, tris, keys, dump, cull_block,
+                        cull_bps, inline_max, chunk_rays) <
+               std::tie(o.n_sensors, o.n_rays, o.total_ch, o.flags, o.n_tris, o.out_dist, o.out_tri, o.tris, o.keys,
+                        o.dump, o.cull_block, o.cull_bps, o.inline_max, o.chunk_rays);
+    }
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct grca_ctx {
+    int device = 0;
+    int n_sm = 152;
+    grca_options opt{};
+    LaunchCfg cfg;
+    cudaStream_t cap_stream = nullptr;
+
+    float* d_tris = nullptr;
+    uint32_t n_tris = 0;
+    size_t tris_cap = 0;  // triangles
+
+    std::vector<SensorHost> sensors;
+    float2* d_ch = nullptr;
+    double2* d_ch64 = nullptr;
+    float2* d_az = nullptr;
+    double2* d_az64 = nullptr;
+    std::vector<uint32_t> ch_off, az_off;
+    bool tables_dirty = true;
+
+    unsigned long long* d_keys = nullptr;
+    unsigned long long* d_keys64 = nullptr;
+    uint32_t* d_flag_bits = nullptr;
+    uint32_t* d_flag_list = nullptr;
+    size_t ray_cap = 0;
+
+    BigPair* d_big = nullptr;
+    PairSetup* d_setups = nullptr;
+    uint4* d_chunks = nullptr;
+    uint2* d_recheck = nullptr;
+    uint32_t* d_qcount = nullptr;
+    unsigned long long* d_counters = nullptr;
+    uint32_t* d_error = nullptr;
+
+    SensorDev* d_sens = nullptr;
+    SensorDev* h_ring = nullptr;
+    cudaEvent_t ring_ev[RING] = {};
+    bool ring_used[RING] = {};
+    int ring_pos = 0;
+
+    float* d_out_dist = nullptr;
+    uint32_t* d_out_tri = nullptr;
+    size_t out_cap = 0;
+
+    uint32_t* dump = nullptr;
+    uint64_t dump_cap = 0;
+    uint32_t* dump_count = nullptr;
+
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, LaunchCfg> tuned;
+
+    uint64_t last_n_rays = 0;
+    uint32_t last_launches = 0;
+    std::string last_err;
+
+    // per-kernel CUDA-event timing (grca_profile_*)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_next = 0;
+    struct Pending {
+        int kernel;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    cudaEvent_t open_ev[K_NUM];
+    double total_ms[K_NUM] = {};
+    uint64_t n_launch[K_NUM] = {};
+};
+
+static cudaEvent_t pool_event(grca_ctx* ctx) {
+    if (ctx->ev_next == ctx->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        ctx->ev_pool.push_back(e);
+    }
+    return ctx->ev_pool[ctx->ev_next++];
+}
+
+static void drain_profile(grca_ctx* ctx) {
+    for (auto& p : ctx->pending) {
+        float ms = 0.f;
+        cudaEventSynchronize(p.b);
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            ctx->total_ms[p.kernel] += ms;
+            ctx->n_launch[p.kernel] += 1;
+        }
+    }
+    ctx->pending.clear();
+    ctx->ev_next = 0;
+}
+
+static void profile_mark(void* user, int kernel, int phase, cudaStream_t st) {
+    grca_ctx* ctx = (grca_ctx*)user;
+    if (ctx->ev_next + 2 > 8192) drain_profile(ctx);
+    cudaEvent_t e = pool_event(ctx);
+    if (!e) return;
+    cudaEventRecord(e, st);
+    if (phase == 0) {
+        ctx->open_ev[kernel] = e;
+    } else {
+        ctx->pending.push_back({kernel, ctx->open_ev[kernel], e});
+    }
+}
+
+static grca_status cuda_fail(grca_ctx* c, cudaError_t e, const char* what) {
+    if (c) c->last_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? GRCA_ERR_OOM : GRCA_ERR_CUDA;
+}
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+static void free_graphs(grca_ctx* ctx) {
+    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+}
+
+static bool valid_axes(const double f[3], const double r[3], const double u[3]) {
+    auto dot = [](const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
+    const double* v[3] = {f, r, u};
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(v[i][k])) return false;
+    for (int i = 0; i < 3; ++i) {
+        if (std::fabs(dot(v[i], v[i]) - 1.0) > 1e-9) return false;
+        for (int k = i + 1; k < 3; ++k)
+            if (std::fabs(dot(v[i], v[k])) > 1e-9) return false;
+    }
+    return true;
+}
+
+extern "C" {
+
+const char* grca_status_string(grca_status s) {
+    switch (s) {
+        case GRCA_OK: return "ok";
+        case GRCA_ERR_INVALID_ARG: return "invalid argument";
+        case GRCA_ERR_OOM: return "out of memory";
+        case GRCA_ERR_CUDA: return "CUDA error";
+        case GRCA_ERR_CAPACITY: return "device work queue capacity exceeded";
+        case GRCA_ERR_TIMEOUT: return "bounded device wait timed out";
+        case GRCA_ERR_NOT_READY: return "not ready (no triangles or sensors)";
+        default: return "unknown status";
+    }
+}
+
+const char* grca_last_cuda_error(grca_ctx* ctx) { return ctx ? ctx->last_err.c_str() : ""; }
+
+grca_status grca_create(grca_ctx** out, int device, const grca_options* opt) {
+    if (!out) return GRCA_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n_dev = 0;
+    if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) return GRCA_ERR_INVALID_ARG;
+    grca_ctx* ctx = new (std::nothrow) grca_ctx();
+    if (!ctx) return GRCA_ERR_OOM;
+    ctx->device = device;
+    if (opt) ctx->opt = *opt;
+    grca_options& o = ctx->opt;
+    if (!o.big_pair_capacity) o.big_pair_capacity = 4u << 20;
+    if (!o.chunk_capacity) o.chunk_capacity = 32u << 20;
+    if (!o.recheck_capacity) o.recheck_capacity = 8u << 20;
+    if (!o.inline_max) o.inline_max = 16;
+    if (!o.chunk_rays) o.chunk_rays = 64;
+    if (!o.cull_block) o.cull_block = 256;
+    if (!o.cull_blocks_per_sm) o.cull_blocks_per_sm = 4;
+    if (o.big_pair_capacity > 0xFFFFFFFFull || o.chunk_capacity > 0xFFFFFFFFull || o.recheck_capacity > 0xFFFFFFFFull ||
+        o.cull_block % 32 || o.cull_block > 256 || o.cull_block < 32 || o.chunk_rays > 4096) {
+        delete ctx;
+        return GRCA_ERR_INVALID_ARG;
+    }
+    ctx->cfg.cull_block = (int)o.cull_block;
+    ctx->cfg.cull_blocks_per_sm = (int)o.cull_blocks_per_sm;
+    ctx->cfg.inline_max = (int)o.inline_max;
+    ctx->cfg.chunk_rays = (int)o.chunk_rays;
+    DeviceGuard g(device);
+    cudaDeviceProp prop;
+    grca_status st = GRCA_OK;
+    auto fail = [&](cudaError_t e, const char* w) {
+        st = cuda_fail(ctx, e, w);
+        return st;
+    };
+    cudaError_t e;
+    if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) fail(e, "cudaGetDeviceProperties");
+    if (st == GRCA_OK) ctx->n_sm = prop.multiProcessorCount;
+    if (st == GRCA_OK && (e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        fail(e, "cudaStreamCreate");
+    if (st == GRCA_OK && (e = cudaMalloc(&ctx->d_big, sizeof(BigPair) * o.big_pair_capacity)) != cudaSuccess)
+        fail(e, "cudaMalloc(big)");
+    if (st == GRCA_OK && (e = cudaMalloc(&ctx->d_setups, sizeof(PairSetup) * o.big_pair_capacity)) != cudaSuccess)
+        fail(e, "cudaMalloc(setups)");
+    if (st == GRCA_OK && (e = cudaMalloc(&ctx->d_chunks, sizeof(uint4) * o.chunk_capacity)) != cudaSuccess)
+        fail(e, "cudaMalloc(chunks)");
+    if (st == GRCA_OK && (e = cudaMalloc(&ctx->d_recheck, sizeof(uint2) * o.recheck_capacity)) != cudaSuccess)
+        fail(e, "cudaMalloc(recheck)");
+    if (st == GRCA_OK && (e = cudaMalloc(&ctx->d_qcount, sizeof(uint32_t) * Q_NUM)) != cudaSuccess)
+        fail(e, "cudaMalloc(qcount)");
+    if (st == GRCA_OK && (e = cudaMalloc(&ctx->d_counters, sizeof(unsigned long long) * C_NUM)) != cudaSuccess)
+        fail(e, "cudaMalloc(counters)");
+    if (st == GRCA_OK && (e = cudaMalloc(&ctx->d_error, sizeof(uint32_t))) != cudaSuccess) fail(e, "cudaMalloc(error)");
+    if (st == GRCA_OK && (e = cudaMalloc(&ctx->d_sens, sizeof(SensorDev) * MAX_SENSORS)) != cudaSuccess)
+        fail(e, "cudaMalloc(sensors)");
+    if (st == GRCA_OK && (e = cudaMallocHost(&ctx->h_ring, sizeof(SensorDev) * MAX_SENSORS * RING)) != cudaSuccess)
+        fail(e, "cudaMallocHost(ring)");
+    for (int k = 0; k < RING; ++k) {
+        ctx->ring_used[k] = false;
+        if (st == GRCA_OK && (e = cudaEventCreateWithFlags(&ctx->ring_ev[k], cudaEventDisableTiming)) != cudaSuccess)
+            fail(e, "cudaEventCreate");
+    }
+    if (st == GRCA_OK) {
+        cudaMemset(ctx->d_qcount, 0, sizeof(uint32_t) * Q_NUM);
+        cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * C_NUM);
+        cudaMemset(ctx->d_error, 0, sizeof(uint32_t));
+        cudaDeviceSynchronize();
+    }
+    if (st != GRCA_OK) {
+        grca_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return GRCA_OK;
+}
+
+void grca_destroy(grca_ctx* ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    if (ctx->cap_stream) cudaStreamSynchronize(ctx->cap_stream);
+    cudaDeviceSynchronize();
+    free_graphs(ctx);
+    cudaFree(ctx->d_tris);
+    cudaFree(ctx->d_ch);
+    cudaFree(ctx->d_ch64);
+    cudaFree(ctx->d_az);
+    cudaFree(ctx->d_az64);
+    cudaFree(ctx->d_keys);
+    cudaFree(ctx->d_keys64);
+    cudaFree(ctx->d_flag_bits);
+    cudaFree(ctx->d_flag_list);
+    cudaFree(ctx->d_big);
+    cudaFree(ctx->d_setups);
+    cudaFree(ctx->d_chunks);
+    cudaFree(ctx->d_recheck);
+    cudaFree(ctx->d_qcount);
+    cudaFree(ctx->d_counters);
+    cudaFree(ctx->d_error);
+    cudaFree(ctx->d_sens);
+    cudaFree(ctx->d_out_dist);
+    cudaFree(ctx->d_out_tri);
+    if (ctx->h_ring) cudaFreeHost(ctx->h_ring);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    for (int k = 0; k < RING; ++k)
+        if (ctx->ring_ev[k]) cudaEventDestroy(ctx->ring_ev[k]);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    delete ctx;
+}
+
+grca_status grca_create_sensor(grca_ctx* ctx, const grca_sensor_desc* d, int32_t* out_id) {
+    if (!ctx || !d || !out_id || !d->elev_rad) return GRCA_ERR_INVALID_ARG;
+    if (d->n_channels < 1 || d->n_channels > (uint32_t)MAX_CHANNELS || d->n_rays < 1 || d->n_rays > (uint32_t)MAX_RAYS)
+        return GRCA_ERR_INVALID_ARG;
+    if (!valid_axes(d->f, d->r, d->u)) return GRCA_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(d->origin[k])) return GRCA_ERR_INVALID_ARG;
+    for (uint32_t j = 0; j < d->n_channels; ++j) {
+        double e = d->elev_rad[j];
+        if (!std::isfinite(e) || std::fabs(e) >= M_PI / 2) return GRCA_ERR_INVALID_ARG;
+        if (j > 0 && !(e > d->elev_rad[j - 1])) return GRCA_ERR_INVALID_ARG;
+    }
+    if (!std::isfinite(d->theta0) || !std::isfinite(d->dtheta) || !(d->dtheta > 0.0)) return GRCA_ERR_INVALID_ARG;
+    if (d->n_rays * d->dtheta > 2 * M_PI + 1e-9) return GRCA_ERR_INVALID_ARG;
+    if (std::fabs(d->theta0) > 4 * M_PI) return GRCA_ERR_INVALID_ARG;
+    if (!(d->d_min >= 0.0) || !(d->d_max >= d->d_min) || !std::isfinite(d->d_min)) return GRCA_ERR_INVALID_ARG;
+    SensorHost s;
+    s.d = *d;
+    s.elev.assign(d->elev_rad, d->elev_rad + d->n_channels);
+    s.d.elev_rad = nullptr;
+    s.full = std::fabs(d->n_rays * d->dtheta - 2 * M_PI) <= 1e-9;
+    ctx->sensors.push_back(std::move(s));
+    ctx->tables_dirty = true;
+    *out_id = (int32_t)ctx->sensors.size() - 1;
+    return GRCA_OK;
+}
+
+grca_status grca_set_sensor_pose(grca_ctx* ctx, int32_t id, const double origin[3], const double f[3],
+                                 const double r[3], const double u[3]) {
+    if (!ctx || !origin || !f || !r || !u || id < 0 || id >= (int32_t)ctx->sensors.size()) return GRCA_ERR_INVALID_ARG;
+    if (!valid_axes(f, r, u)) return GRCA_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(origin[k])) return GRCA_ERR_INVALID_ARG;
+    grca_sensor_desc& d = ctx->sensors[id].d;
+    for (int k = 0; k < 3; ++k) {
+        d.origin[k] = origin[k];
+        d.f[k] = f[k];
+        d.r[k] = r[k];
+        d.u[k] = u[k];
+    }
+    return GRCA_OK;
+}
+
+static grca_status copy_in(grca_ctx* ctx, float* dst, const float* src, size_t n_floats, int where,
+                           cudaStream_t st) {
+    if (n_floats == 0) return GRCA_OK;
+    cudaMemcpyKind kind = where == GRCA_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(dst, src, n_floats * sizeof(float), kind, st));
+    return GRCA_OK;
+}
+
+grca_status grca_upload_triangles(grca_ctx* ctx, const float* xyz, uint32_t n_tris, int where, void* stream) {
+    if (!ctx || (!xyz && n_tris) || (where != GRCA_MEM_HOST && where != GRCA_MEM_DEVICE)) return GRCA_ERR_INVALID_ARG;
+    if (n_tris > 0x7FFFFFFFu) return GRCA_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_tris > ctx->tris_cap) {
+        CK(cudaStreamSynchronize(st));
+        cudaFree(ctx->d_tris);
+        ctx->d_tris = nullptr;
+        ctx->tris_cap = 0;
+        // + 4 floats of tail padding: the culling pass stages whole float4s
+        CK(cudaMalloc(&ctx->d_tris, (9ull * n_tris + 16) * sizeof(float)));
+        CK(cudaMemsetAsync(ctx->d_tris, 0, (9ull * n_tris + 16) * sizeof(float), st));
+        ctx->tris_cap = n_tris;
+        free_graphs(ctx);
+    }
+    ctx->n_tris = n_tris;
+    return copy_in(ctx, ctx->d_tris, xyz, 9ull * n_tris, where, st);
+}
+
+grca_status grca_update_vertices(grca_ctx* ctx, const float* xyz, uint32_t first, uint32_t n_tris, int where,
+                                 void* stream) {
+    if (!ctx || (!xyz && n_tris) || (where != GRCA_MEM_HOST && where != GRCA_MEM_DEVICE)) return GRCA_ERR_INVALID_ARG;
+    if ((uint64_t)first + n_tris > ctx->n_tris) return GRCA_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    return copy_in(ctx, ctx->d_tris + 9ull * first, xyz, 9ull * n_tris, where, (cudaStream_t)stream);
+}
+
+grca_status grca_set_debug_dump(grca_ctx* ctx, uint32_t* pairs, uint64_t cap, uint32_t* counter) {
+    if (!ctx) return GRCA_ERR_INVALID_ARG;
+    if ((pairs == nullptr) != (counter == nullptr) || cap > 0xFFFFFFFFull) return GRCA_ERR_INVALID_ARG;
+    ctx->dump = pairs;
+    ctx->dump_cap = pairs ? cap : 0;
+    ctx->dump_count = counter;
+    return GRCA_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// cast orchestration
+// ---------------------------------------------------------------------------
+static grca_status ensure_tables(grca_ctx* ctx, cudaStream_t st) {
+    if (!ctx->tables_dirty) return GRCA_OK;
+    std::vector<float2> ch;
+    std::vector<double2> ch64;
+    std::vector<float2> az;
+    std::vector<double2> az64;
+    ctx->ch_off.clear();
+    ctx->az_off.clear();
+    for (const SensorHost& s : ctx->sensors) {
+        ctx->ch_off.push_back((uint32_t)ch.size());
+        for (double e : s.elev) {
+            double sn = std::sin(e), cs = std::cos(e);
+            ch.push_back(make_float2((float)sn, (float)cs));
+            ch64.push_back(make_double2(sn, cs));
+        }
+        ctx->az_off.push_back((uint32_t)az.size());
+        for (uint32_t i = 0; i < s.d.n_rays; ++i) {
+            double th = s.d.theta0 + (double)i * s.d.dtheta;
+            double sn = std::sin(th), cs = std::cos(th);
+            az.push_back(make_float2((float)sn, (float)cs));
+            az64.push_back(make_double2(sn, cs));
+        }
+    }
+    CK(cudaStreamSynchronize(st));
+    cudaFree(ctx->d_ch);
+    cudaFree(ctx->d_ch64);
+    cudaFree(ctx->d_az);
+    cudaFree(ctx->d_az64);
+    ctx->d_ch = nullptr;
+    ctx->d_ch64 = nullptr;
+    ctx->d_az = nullptr;
+    ctx->d_az64 = nullptr;
+    CK(cudaMalloc(&ctx->d_ch, sizeof(float2) * std::max<size_t>(ch.size(), 1)));
+    CK(cudaMalloc(&ctx->d_ch64, sizeof(double2) * std::max<size_t>(ch.size(), 1)));
+    CK(cudaMalloc(&ctx->d_az, sizeof(float2) * std::max<size_t>(az.size(), 1)));
+    CK(cudaMalloc(&ctx->d_az64, sizeof(double2) * std::max<size_t>(az.size(), 1)));
+    CK(cudaMemcpy(ctx->d_ch, ch.data(), sizeof(float2) * ch.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_ch64, ch64.data(), sizeof(double2) * ch.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_az, az.data(), sizeof(float2) * az.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_az64, az64.data(), sizeof(double2) * az.size(), cudaMemcpyHostToDevice));
+    ctx->tables_dirty = false;
+    free_graphs(ctx);
+    return GRCA_OK;
+}
+
+static grca_status ensure_rays(grca_ctx* ctx, size_t n_rays, cudaStream_t st) {
+    if (n_rays <= ctx->ray_cap) return GRCA_OK;
+    CK(cudaStreamSynchronize(st));
+    cudaFree(ctx->d_keys);
+    cudaFree(ctx->d_keys64);
+    cudaFree(ctx->d_flag_bits);
+    cudaFree(ctx->d_flag_list);
+    ctx->d_keys = ctx->d_keys64 = nullptr;
+    ctx->d_flag_bits = ctx->d_flag_list = nullptr;
+    ctx->ray_cap = 0;
+    CK(cudaMalloc(&ctx->d_keys, sizeof(unsigned long long) * n_rays));
+    CK(cudaMalloc(&ctx->d_keys64, sizeof(unsigned long long) * n_rays));
+    CK(cudaMalloc(&ctx->d_flag_bits, sizeof(uint32_t) * ((n_rays + 31) / 32)));
+    CK(cudaMalloc(&ctx->d_flag_list, sizeof(uint32_t) * n_rays));
+    ctx->ray_cap = n_rays;
+    free_graphs(ctx);
+    return GRCA_OK;
+}
+
+static void fill_sensor(const grca_ctx* ctx, int id, uint32_t ray_off, SensorDev& s) {
+    const SensorHost& h = ctx->sensors[id];
+    const grca_sensor_desc& d = h.d;
+    memset(&s, 0, sizeof(s));
+    for (int k = 0; k < 3; ++k) {
+        s.o64[k] = d.origin[k];
+        s.B64[k] = d.f[k];
+        s.B64[3 + k] = d.r[k];
+        s.B64[6 + k] = d.u[k];
+        float hi = (float)d.origin[k];
+        s.o_hi[k] = hi;
+        s.o_lo[k] = (float)(d.origin[k] - (double)hi);
+    }
+    for (int k = 0; k < 9; ++k) s.B[k] = (float)s.B64[k];
+    s.d_min64 = d.d_min;
+    s.d_max64 = d.d_max;
+    s.theta0 = (float)d.theta0;
+    s.dtheta = (float)d.dtheta;
+    s.inv_dtheta = (float)(1.0 / d.dtheta);
+    s.d_min = (float)d.d_min;
+    s.d_max = std::isfinite(d.d_max) ? (float)d.d_max : INFINITY;
+    s.period = (float)(2 * M_PI / d.dtheta);
+    s.n_ch = d.n_channels;
+    s.n_rays = d.n_rays;
+    s.ch_off = ctx->ch_off[id];
+    s.az_off = ctx->az_off[id];
+    s.ray_off = ray_off;
+    s.full = h.full ? 1u : 0u;
+    s.has_range = (d.d_min > 0.0 || std::isfinite(d.d_max)) ? 1u : 0u;
+}
+
+static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, float* out_dist, uint32_t* out_tri,
+                                uint32_t flags, cudaStream_t st, CastArgs& a) {
+    if (!ids || n < 1 || n > (uint32_t)MAX_SENSORS || !out_dist || !out_tri) return GRCA_ERR_INVALID_ARG;
+    if (flags & ~0x1Fu) return GRCA_ERR_INVALID_ARG;
+    if ((flags & GRCA_CAST_DUMP_CANDIDATES) && !ctx->dump) return GRCA_ERR_INVALID_ARG;
+    for (uint32_t k = 0; k < n; ++k)
+        if (ids[k] < 0 || ids[k] >= (int32_t)ctx->sensors.size()) return GRCA_ERR_INVALID_ARG;
+    if (!ctx->d_tris && ctx->n_tris) return GRCA_ERR_NOT_READY;
+    grca_status rs = ensure_tables(ctx, st);
+    if (rs != GRCA_OK) return rs;
+    uint64_t total = 0, total_ch = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        const grca_sensor_desc& d = ctx->sensors[ids[k]].d;
+        total += (uint64_t)d.n_channels * d.n_rays;
+        total_ch += d.n_channels;
+    }
+    if (total >= 0xFFFFFFFFull || total_ch > 8192) return GRCA_ERR_INVALID_ARG;
+    rs = ensure_rays(ctx, total, st);
+    if (rs != GRCA_OK) return rs;
+    // stage the descriptors through a pinned ring slot (stream-ordered copy)
+    int slot = ctx->ring_pos;
+    ctx->ring_pos = (ctx->ring_pos + 1) % RING;
+    if (ctx->ring_used[slot]) CK(cudaEventSynchronize(ctx->ring_ev[slot]));
+    SensorDev* h = ctx->h_ring + (size_t)slot * MAX_SENSORS;
+    uint32_t off = 0, ch_loc = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        fill_sensor(ctx, ids[k], off, h[k]);
+        h[k].ch_loc = ch_loc;
+        off += ctx->sensors[ids[k]].d.n_channels * ctx->sensors[ids[k]].d.n_rays;
+        ch_loc += ctx->sensors[ids[k]].d.n_channels;
+    }
+    CK(cudaMemcpyAsync(ctx->d_sens, h, sizeof(SensorDev) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(ctx->ring_ev[slot], st));
+    ctx->ring_used[slot] = true;
+
+    memset(&a, 0, sizeof(a));
+    a.tris = ctx->d_tris;
+    a.n_tris = ctx->n_tris;
+    a.n_sensors = n;
+    a.sensors = ctx->d_sens;
+    a.ch_sc = ctx->d_ch;
+    a.ch_sc64 = ctx->d_ch64;
+    a.az_sc = ctx->d_az;
+    a.az_sc64 = ctx->d_az64;
+    a.total_ch = (uint32_t)total_ch;
+    a.n_rays_total = (uint32_t)total;
+    a.keys = ctx->d_keys;
+    a.keys64 = ctx->d_keys64;
+    a.flag_bits = ctx->d_flag_bits;
+    a.flag_list = ctx->d_flag_list;
+    a.flag_cap = (uint32_t)ctx->ray_cap;
+    a.big_cap = (uint32_t)ctx->opt.big_pair_capacity;
+    a.big = ctx->d_big;
+    a.setups = ctx->d_setups;
+    a.chunks = ctx->d_chunks;
+    a.chunk_cap = (uint32_t)ctx->opt.chunk_capacity;
+    a.recheck_cap = (uint32_t)ctx->opt.recheck_capacity;
+    a.recheck = ctx->d_recheck;
+    a.qcount = ctx->d_qcount;
+    a.counters = ctx->d_counters;
+    a.error = ctx->d_error;
+    a.flags = flags;
+    a.dump = ctx->dump;
+    a.dump_cap = (uint32_t)ctx->dump_cap;
+    a.dump_count = ctx->dump_count;
+    a.out_dist = out_dist;
+    a.out_tri = out_tri;
+    return GRCA_OK;
+}
+
+static LaunchCfg cfg_for(grca_ctx* ctx, const CastArgs& a) {
+    auto key = std::make_tuple(a.n_sensors, a.n_rays_total, a.n_tris, a.flags & 0x7u);
+    auto it = ctx->tuned.find(key);
+    return it == ctx->tuned.end() ? ctx->cfg : it->second;
+}
+
+static grca_status run_frame(grca_ctx* ctx, CastArgs& a, const LaunchCfg& cfg, cudaStream_t st, bool use_graph) {
+    a.inline_max = (uint32_t)cfg.inline_max;
+    a.chunk_rays = (uint32_t)cfg.chunk_rays;
+    if (ctx->profiling) {
+        KernelMarks mk{profile_mark, ctx};
+        ctx->last_launches = (uint32_t)launch_frame(a, cfg, ctx->n_sm, st, &mk);
+        CK(cudaGetLastError());
+        return GRCA_OK;
+    }
+    if (!use_graph) {
+        ctx->last_launches = (uint32_t)launch_frame(a, cfg, ctx->n_sm, st);
+        CK(cudaGetLastError());
+        return GRCA_OK;
+    }
+    GraphKey k{a.n_sensors, a.n_rays_total, a.total_ch, a.flags, a.n_tris, a.out_dist, a.out_tri, a.tris, a.keys,
+               a.dump, cfg.cull_block, cfg.cull_blocks_per_sm, cfg.inline_max, cfg.chunk_rays};
+    auto it = ctx->graphs.find(k);
+    if (it == ctx->graphs.end()) {
+        if (ctx->graphs.size() >= 32) free_graphs(ctx);
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int nl = launch_frame(a, cfg, ctx->n_sm, ctx->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+        cudaGraphExec_t exec;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        it = ctx->graphs.emplace(k, exec).first;
+        ctx->last_launches = (uint32_t)nl;
+    }
+    CK(cudaGraphLaunch(it->second, st));
+    return GRCA_OK;
+}
+
+extern "C" {
+
+grca_status grca_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, float* out_dist, uint32_t* out_tri,
+                      uint32_t flags, void* stream) {
+    if (!ctx) return GRCA_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CastArgs a;
+    grca_status rs = prepare_cast(ctx, ids, n, out_dist, out_tri, flags, st, a);
+    if (rs != GRCA_OK) return rs;
+    ctx->last_n_rays = a.n_rays_total;
+    return run_frame(ctx, a, cfg_for(ctx, a), st, (flags & GRCA_CAST_GRAPH) != 0);
+}
+
+grca_status grca_cast_host(grca_ctx* ctx, const int32_t* ids, uint32_t n, const float* xyz_dyn, uint32_t first_dyn,
+                           uint32_t n_dyn, float* out_dist_h, uint32_t* out_tri_h, uint32_t flags, void* stream) {
+    if (!ctx || !out_dist_h || !out_tri_h || (!xyz_dyn && n_dyn)) return GRCA_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_dyn) {
+        grca_status rs = grca_update_vertices(ctx, xyz_dyn, first_dyn, n_dyn, GRCA_MEM_HOST, stream);
+        if (rs != GRCA_OK) return rs;
+    }
+    uint64_t total = 0;
+    if (!ids || n < 1 || n > (uint32_t)MAX_SENSORS) return GRCA_ERR_INVALID_ARG;
+    for (uint32_t k = 0; k < n; ++k) {
+        if (ids[k] < 0 || ids[k] >= (int32_t)ctx->sensors.size()) return GRCA_ERR_INVALID_ARG;
+        total += (uint64_t)ctx->sensors[ids[k]].d.n_channels * ctx->sensors[ids[k]].d.n_rays;
+    }
+    if (total > ctx->out_cap) {
+        CK(cudaStreamSynchronize(st));
+        cudaFree(ctx->d_out_dist);
+        cudaFree(ctx->d_out_tri);
+        ctx->d_out_dist = nullptr;
+        ctx->d_out_tri = nullptr;
+        ctx->out_cap = 0;
+        CK(cudaMalloc(&ctx->d_out_dist, sizeof(float) * total));
+        CK(cudaMalloc(&ctx->d_out_tri, sizeof(uint32_t) * total));
+        ctx->out_cap = total;
+        free_graphs(ctx);
+    }
+    grca_status rs = grca_cast(ctx, ids, n, ctx->d_out_dist, ctx->d_out_tri, flags, stream);
+    if (rs != GRCA_OK) return rs;
+    CK(cudaMemcpyAsync(out_dist_h, ctx->d_out_dist, sizeof(float) * total, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(out_tri_h, ctx->d_out_tri, sizeof(uint32_t) * total, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return GRCA_OK;
+}
+
+grca_status grca_get_stats(grca_ctx* ctx, grca_stats* out, void* stream) {
+    if (!ctx || !out) return GRCA_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long c[C_NUM];
+    uint32_t err = 0;
+    CK(cudaMemcpyAsync(c, ctx->d_counters, sizeof(c), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&err, ctx->d_error, sizeof(err), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    memset(out, 0, sizeof(*out));
+    out->pairs = c[C_PAIRS];
+    out->pairs_live = c[C_PAIRS_LIVE];
+    out->candidates = c[C_CAND];
+    out->candidates_inline = c[C_CAND_INLINE];
+    out->big_pairs = c[C_BIG];
+    out->chunks = c[C_CHUNKS];
+    out->tests = c[C_TESTS];
+    out->hits = c[C_HITS];
+    out->uncertain = c[C_UNCERTAIN];
+    out->ties = c[C_TIES];
+    out->flagged_rays = c[C_FLAGGED];
+    out->recheck_pairs = c[C_RECHECK];
+    out->n_rays = ctx->last_n_rays;
+    out->device_error = err;
+    return err ? GRCA_ERR_CAPACITY : GRCA_OK;
+}
+
+uint32_t grca_last_launch_count(grca_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+grca_status grca_profile_enable(grca_ctx* ctx, int enable) {
+    if (!ctx) return GRCA_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    drain_profile(ctx);
+    ctx->profiling = enable != 0;
+    for (int k = 0; k < K_NUM; ++k) {
+        ctx->total_ms[k] = 0.0;
+        ctx->n_launch[k] = 0;
+    }
+    return GRCA_OK;
+}
+
+grca_status grca_profile_read(grca_ctx* ctx, uint32_t max, const char** names, uint64_t* launches, double* total_ms,
+                              uint32_t* n_out) {
+    if (!ctx || !n_out || (max && (!names || !launches || !total_ms))) return GRCA_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    drain_profile(ctx);
+    uint32_t n = std::min<uint32_t>(max, (uint32_t)K_NUM);
+    for (uint32_t k = 0; k < n; ++k) {
+        names[k] = kKernelNames[k];
+        launches[k] = ctx->n_launch[k];
+        total_ms[k] = ctx->total_ms[k];
+    }
+    *n_out = (uint32_t)K_NUM;
+    return GRCA_OK;
+}
+
+grca_status grca_autotune(grca_ctx* ctx, const int32_t* ids, uint32_t n, float* out_dist, uint32_t* out_tri,
+                          uint32_t flags, void* stream, float* out_ms) {
+    if (!ctx) return GRCA_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CastArgs a;
+    uint32_t fl = flags & ~(uint32_t)(GRCA_CAST_GRAPH | GRCA_CAST_DUMP_CANDIDATES);
+    grca_status rs = prepare_cast(ctx, ids, n, out_dist, out_tri, fl, st, a);
+    if (rs != GRCA_OK) return rs;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto time_cfg = [&](const LaunchCfg& c, float& ms) -> grca_status {
+        float best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            CastArgs b = a;
+            CK(cudaEventRecord(e0, st));
+            grca_status r = run_frame(ctx, b, c, st, false);
+            if (r != GRCA_OK) return r;
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            uint32_t err = 0;
+            CK(cudaMemcpy(&err, ctx->d_error, sizeof(err), cudaMemcpyDeviceToHost));
+            float t;
+            CK(cudaEventElapsedTime(&t, e0, e1));
+            if (err) t = 1e30f;  // a configuration that overflows a queue is not eligible
+            if (rep > 0) best = std::min(best, t);
+        }
+        ms = best;
+        return GRCA_OK;
+    };
+    LaunchCfg best = cfg_for(ctx, a);
+    float best_ms;
+    rs = time_cfg(best, best_ms);
+    // coordinate descent over the launch parameters
+    const int inl[] = {4, 8, 16, 32, 64, 128};
+    const int chk[] = {32, 64, 128, 256};
+    const int blk[] = {128, 256};
+    const int bps[] = {2, 4, 8};
+    for (int pass = 0; pass < 2 && rs == GRCA_OK; ++pass) {
+        for (int v : inl) {
+            LaunchCfg c = best;
+            c.inline_max = v;
+            float ms;
+            if ((rs = time_cfg(c, ms)) != GRCA_OK) break;
+            if (ms < best_ms) best_ms = ms, best = c;
+        }
+        for (int v : chk) {
+            LaunchCfg c = best;
+            c.chunk_rays = v;
+            float ms;
+            if ((rs = time_cfg(c, ms)) != GRCA_OK) break;
+            if (ms < best_ms) best_ms = ms, best = c;
+        }
+        for (int b : blk)
+            for (int p : bps) {
+                LaunchCfg c = best;
+                c.cull_block = b;
+                c.cull_blocks_per_sm = p;
+                float ms;
+                if ((rs = time_cfg(c, ms)) != GRCA_OK) break;
+                if (ms < best_ms) best_ms = ms, best = c;
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rs != GRCA_OK) return rs;
+    ctx->tuned[std::make_tuple(a.n_sensors, a.n_rays_total, a.n_tris, fl & 0x7u)] = best;
+    if (out_ms) *out_ms = best_ms;
+    // leave the outputs holding a valid frame from the chosen configuration
+    CastArgs b = a;
+    return run_frame(ctx, b, best, st, false);
+}
+
+}  // extern "C"

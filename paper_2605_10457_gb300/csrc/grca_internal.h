@@ -1,0 +1,140 @@
+// Internal structures shared by the host runtime (grca_api.cu) and the
+// kernels (grca_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace grca {
+
+// Closest-hit key: (float bits of t) << 32 | triangle id.  For t > 0 the float
+// bits order like the floats, so a u64 min is a lexicographic (t, id) min: the
+// 64-bit widening of the order-preserving float->u32 map of Sec. A.5.2 (for
+// t >= 0 the map is the identity on the bits).  Miss = (+inf, 0xFFFFFFFF).
+constexpr unsigned long long KEY_MISS = 0x7F800000FFFFFFFFull;
+constexpr uint32_t NO_HIT = 0xFFFFFFFFu;
+
+constexpr int MAX_SENSORS = 64;
+constexpr int MAX_CHANNELS = 1024;
+constexpr int MAX_RAYS = 32768;
+
+// queue counters (device uint32[8])
+enum { Q_BIG = 0, Q_CHUNK = 1, Q_RECHECK = 2, Q_FLAG = 3, Q_DUMP = 4, Q_NUM = 8 };
+// statistics counters (device u64[16])
+enum {
+    C_PAIRS = 0, C_PAIRS_LIVE, C_CAND, C_CAND_INLINE, C_BIG, C_CHUNKS, C_TESTS, C_HITS,
+    C_UNCERTAIN, C_TIES, C_FLAGGED, C_RECHECK, C_NUM = 16
+};
+// device error bits
+enum { ERR_BIG_CAP = 1, ERR_CHUNK_CAP = 2, ERR_RECHECK_CAP = 4, ERR_FLAG_CAP = 8, ERR_DUMP_CAP = 16 };
+
+// One sensor of a cast, as the kernels read it.  FP64 first (alignment).
+struct SensorDev {
+    double o64[3];
+    double B64[9];        // rows f, r, u
+    double d_min64, d_max64;
+    float o_hi[3], o_lo[3];  // origin = o_hi + o_lo (float pair)
+    float B[9];           // rows f, r, u (FP32)
+    float theta0, dtheta, inv_dtheta;
+    float d_min, d_max;
+    float period;         // 2*pi/dtheta, in rays
+    uint32_t n_ch, n_rays;
+    uint32_t ch_off;      // offset of this sensor's channel table
+    uint32_t az_off;      // offset of this sensor's azimuth table
+    uint32_t ray_off;     // global ray offset O_n
+    uint32_t full;        // 1: the azimuth grid closes the circle (period == n_rays)
+    uint32_t has_range;   // 1: d_min > 0 or d_max finite
+    uint32_t ch_loc;      // offset of this sensor's channels in the cast-local (shared-memory) table
+};
+
+// Per (triangle, sensor) test setup: everything the per-candidate
+// ray-triangle test needs (emitter frame), 80 bytes.
+struct __align__(16) PairSetup {
+    float m[9];      // folded edge-plane normals: forward hit <=> all d.m_k >= 0
+    float tau[3];    // per-edge FP32 error bound of d.m_k
+    float n[3];      // emitter-frame normal (v1-v0)x(v2-v0)
+    float det;       // (v0-o).n  (world frame); t = det / (d.n)
+    float err_det;   // relative FP32 error bound of det
+    uint32_t state;  // bit0: |det| within its error bound (facing / orientation uncertain)
+    float G[3];      // err(d.n) <= sum_i |d_i| G_i
+    float pad_;
+};
+
+// A (triangle, sensor) pair deferred to the per-channel span pass (32 bytes).
+struct __align__(16) BigPair {
+    uint32_t tri;
+    uint16_t sensor, flags;   // flags bit0: vertical axis pierces (full azimuth)
+    uint16_t j_lo, j_hi;      // channel span (inclusive)
+    int32_t u_lo;             // first ray of the pair span (unwrapped ray units)
+    uint32_t n_r;             // rays in the pair span
+    float a0;                 // ray-unit coordinate of vertex 0's azimuth (normalised)
+    uint32_t pad_[2];
+};
+
+struct Chunk {  // uint4 in memory
+    uint32_t bp;      // big pair index
+    uint32_t j;       // channel
+    uint32_t r0;      // first ray (0..n_rays-1)
+    uint32_t count;   // rays (wrapping modulo n_rays)
+};
+
+struct CastArgs {
+    const float* tris;
+    uint32_t n_tris;
+    uint32_t n_sensors;
+    const SensorDev* sensors;
+    const float2* ch_sc;      // (sin, cos) of channel elevations, FP32
+    const double2* ch_sc64;
+    const float2* az_sc;      // (sin, cos) of ray azimuths, FP32
+    const double2* az_sc64;
+    uint32_t total_ch;
+    uint32_t n_rays_total;
+    unsigned long long* keys;
+    unsigned long long* keys64;
+    uint32_t* flag_bits;
+    uint32_t* flag_list;
+    uint32_t flag_cap;
+    uint32_t big_cap;
+    BigPair* big;
+    PairSetup* setups;
+    uint4* chunks;
+    uint32_t chunk_cap;
+    uint32_t recheck_cap;
+    uint2* recheck;
+    uint32_t* qcount;
+    unsigned long long* counters;
+    uint32_t* error;
+    uint32_t flags;
+    uint32_t inline_max;
+    uint32_t chunk_rays;
+    uint32_t dump_cap;
+    uint32_t* dump;           // (ray, tri) pairs
+    uint32_t* dump_count;
+    float* out_dist;
+    uint32_t* out_tri;
+};
+
+struct LaunchCfg {
+    int cull_block = 256;
+    int cull_blocks_per_sm = 4;
+    int inline_max = 16;
+    int chunk_rays = 64;
+    int test_block = 256;
+};
+
+// kernels of one frame, in launch order
+enum { K_INIT = 0, K_CULL, K_EXPAND, K_TEST, K_RECHECK_RAYS, K_RECHECK_PAIRS, K_DECODE, K_NUM };
+extern const char* const kKernelNames[K_NUM];
+
+// optional per-kernel hook: called with phase 0 before and phase 1 after each
+// kernel launch, on the launching stream (used for CUDA-event timing)
+struct KernelMarks {
+    void (*fn)(void* user, int kernel, int phase, cudaStream_t st);
+    void* user;
+};
+
+// launcher (grca_kernels.cu); returns the number of kernels launched
+int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t st,
+                 const KernelMarks* marks = nullptr);
+size_t cull_smem_bytes(const CastArgs& a, const LaunchCfg& cfg);
+
+}  // namespace grca

@@ -1,0 +1,1030 @@
+// GRCA hot path kernels for sm_103a (GB300).
+//
+// Per frame (one stream, no host round trip; every kernel reads its work
+// count from device memory, so the sequence is capturable as a CUDA graph):
+//   k_init     key init (+inf, no id), clear the per-ray flag bits and queue
+//              counters (Sec. A.5.1 ray-setup pass).
+//   k_cull     persistent over triangles x sensors: emitter transform,
+//              back-face / range culls (App. A.4.1 Step 1), channel span from
+//              the exact elevation extent (replaces the binary search of
+//              Sec. 3.6), azimuth span from the vertex projections
+//              (Sec. 3.7), then either inline tests (small spans) or a
+//              warp-aggregated append to the deferred queue (App. A.6, BAT
+//              list with ballot/popc allocation).
+//   k_expand   deferred pairs: per-channel cone/plane crossings give exact
+//              per-channel azimuth spans (Sec. 3.5, App. A.4.2 Step 1);
+//              rows are cut into fixed-size chunks of a device work queue.
+//   k_test     one warp per chunk: watertight FP32 test + closest-hit key.
+//   k_recheck_*  FP64 re-test of every ray the FP32 pass flagged.
+//   k_decode   key -> (distance, triangle id) (Sec. A.5.1 output pass).
+//
+// Ray-triangle test.  The paper uses Moller-Trumbore (App. A.4.1 Step 5).
+// Here the test is watertight: edge functions E_k = d . (a_k x b_k) of the
+// planes through the origin and each edge (a_k, b_k vertices relative to the
+// origin, emitter frame).  Each shared edge is evaluated from a canonical
+// (lexicographically smaller) base vertex with explicitly rounded arithmetic,
+// so two triangles sharing an edge get bitwise-opposite edge functions and no
+// ray passes between them.  t = ((v0-o).n) / (d.n).
+#include <cooperative_groups.h>
+#include <algorithm>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "grca_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace grca {
+
+// ---------------------------------------------------------------------------
+// constants of the FP32 pass
+// ---------------------------------------------------------------------------
+constexpr float U32 = 5.9604645e-08f;   // unit roundoff 2^-24
+constexpr float EPS_S = 4e-6f;          // elevation padding (sine space)
+constexpr float EPS_T = 4e-6f;          // azimuth padding (radians) + per-vertex term
+constexpr float EPS_ROW = 2e-5f;        // per-channel crossing azimuth padding (radians)
+constexpr float PADR = 2e-3f;           // ray-unit padding
+constexpr float TAU_T = 4e-6f;          // max relative FP32 error of a committed t
+constexpr float BETA = 1e-5f;           // tie band (>= 2*TAU_T)
+
+// ---------------------------------------------------------------------------
+// explicitly rounded vector helpers: no contraction, bitwise reproducible
+// in every kernel that calls them
+// ---------------------------------------------------------------------------
+struct V3 {
+    float x, y, z;
+};
+__device__ __forceinline__ V3 vsub(V3 a, V3 b) { return {__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z)}; }
+__device__ __forceinline__ float vdot(V3 a, V3 b) {
+    return __fmaf_rn(a.x, b.x, __fmaf_rn(a.y, b.y, __fmul_rn(a.z, b.z)));
+}
+__device__ __forceinline__ V3 vcross(V3 a, V3 b) {
+    return {__fsub_rn(__fmul_rn(a.y, b.z), __fmul_rn(a.z, b.y)), __fsub_rn(__fmul_rn(a.z, b.x), __fmul_rn(a.x, b.z)),
+            __fsub_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x))};
+}
+__device__ __forceinline__ V3 vneg(V3 a) { return {-a.x, -a.y, -a.z}; }
+__device__ __forceinline__ float vnorm(V3 a) { return sqrtf(vdot(a, a)); }
+__device__ __forceinline__ V3 rotB(const float* B, V3 w) {
+    return {vdot({B[0], B[1], B[2]}, w), vdot({B[3], B[4], B[5]}, w), vdot({B[6], B[7], B[8]}, w)};
+}
+__device__ __forceinline__ bool lex_less(V3 a, V3 b) {
+    return a.x < b.x || (a.x == b.x && (a.y < b.y || (a.y == b.y && a.z < b.z)));
+}
+__device__ __forceinline__ float cross2(V3 a, V3 b) { return a.x * b.y - a.y * b.x; }
+__device__ __forceinline__ float dot2(V3 a, V3 b) { return a.x * b.x + a.y * b.y; }
+__device__ __forceinline__ int imod(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+// ---------------------------------------------------------------------------
+// per-triangle world-frame data (independent of the sensor)
+// ---------------------------------------------------------------------------
+struct TriW {
+    V3 v[3];
+    V3 E[3];     // canonical edge vectors V_other - V_base
+    int base[3]; // base vertex index of edge k
+    float sg[3]; // +1 if the canonical direction follows the winding (k -> k+1)
+    V3 n;        // (v1-v0)x(v2-v0)
+    V3 N;        // |products| of the cross product terms (error model)
+};
+
+__device__ __forceinline__ void tri_world(const float* t9, TriW& T) {
+    T.v[0] = {t9[0], t9[1], t9[2]};
+    T.v[1] = {t9[3], t9[4], t9[5]};
+    T.v[2] = {t9[6], t9[7], t9[8]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int k1 = k == 2 ? 0 : k + 1;
+        bool fwd = !lex_less(T.v[k1], T.v[k]);
+        T.base[k] = fwd ? k : k1;
+        T.sg[k] = fwd ? 1.f : -1.f;
+        T.E[k] = fwd ? vsub(T.v[k1], T.v[k]) : vsub(T.v[k], T.v[k1]);
+    }
+    V3 e1 = vsub(T.v[1], T.v[0]), e2 = vsub(T.v[2], T.v[0]);
+    T.n = vcross(e1, e2);
+    T.N = {fabsf(e1.y * e2.z) + fabsf(e1.z * e2.y), fabsf(e1.z * e2.x) + fabsf(e1.x * e2.z),
+           fabsf(e1.x * e2.y) + fabsf(e1.y * e2.x)};
+}
+
+// vertices relative to the origin (world) and in the emitter frame
+__device__ __forceinline__ V3 rel_origin(const SensorDev& S, V3 v) {
+    return vsub(vsub(v, {S.o_hi[0], S.o_hi[1], S.o_hi[2]}), {S.o_lo[0], S.o_lo[1], S.o_lo[2]});
+}
+
+// ---------------------------------------------------------------------------
+// test setup of one (triangle, sensor) pair
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void make_setup(const SensorDev& S, const TriW& T, const V3 w[3], const V3 p[3],
+                                           float det, float err_det_abs, PairSetup& st) {
+    bool unc = fabsf(det) <= err_det_abs;
+    float fold = det < 0.f ? -1.f : 1.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        V3 e = rotB(S.B, T.E[k]);
+        V3 pb = p[T.base[k]];
+        V3 m = vcross(pb, e);
+        float f = T.sg[k] * fold;
+        if (f < 0.f) m = vneg(m);
+        st.m[3 * k + 0] = m.x;
+        st.m[3 * k + 1] = m.y;
+        st.m[3 * k + 2] = m.z;
+        st.tau[k] = U32 * (12.f * vnorm(pb) * vnorm(e) + 6.f * vnorm(m)) + 1e-30f;
+    }
+    V3 ne = rotB(S.B, T.n);
+    st.n[0] = ne.x;
+    st.n[1] = ne.y;
+    st.n[2] = ne.z;
+    st.det = det;
+    st.err_det = det != 0.f ? err_det_abs / fabsf(det) : 1.f;
+    st.state = unc ? 1u : 0u;
+    float an[3] = {fabsf(T.n.x), fabsf(T.n.y), fabsf(T.n.z)};
+    float aN[3] = {T.N.x, T.N.y, T.N.z};
+    float ane[3] = {fabsf(ne.x), fabsf(ne.y), fabsf(ne.z)};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float g = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) g += fabsf(S.B[3 * i + k]) * (3.f * an[k] + 3.f * aN[k]);
+        st.G[i] = U32 * (g + 6.f * ane[i]);
+    }
+    st.pad_ = 0.f;
+}
+
+__device__ __forceinline__ float det_error(const V3& w0, const TriW& T) {
+    return U32 * (fabsf(w0.x) * (3.f * T.N.x + 4.f * fabsf(T.n.x)) + fabsf(w0.y) * (3.f * T.N.y + 4.f * fabsf(T.n.y)) +
+                  fabsf(w0.z) * (3.f * T.N.z + 4.f * fabsf(T.n.z))) + 1e-35f;
+}
+
+// ---------------------------------------------------------------------------
+// per-candidate test
+// ---------------------------------------------------------------------------
+enum { T_MISS = 0, T_HIT = 1, T_UNCERTAIN = 2 };
+
+__device__ __forceinline__ V3 ray_dir(float2 ch, float2 az) {
+    // Eq. ray_dir in the emitter frame: (cos th cos ph, sin th cos ph, sin ph); (x=sin, y=cos)
+    return {__fmul_rn(az.y, ch.y), __fmul_rn(az.x, ch.y), ch.x};
+}
+
+// FP32 test.  Plain mode: inclusive edge test, T_HIT or T_MISS.  Recheck mode
+// additionally returns T_UNCERTAIN when the FP32 decision or t is not
+// guaranteed; *t_err receives the relative error bound of t.
+template <bool RECHECK>
+__device__ __forceinline__ int test_fp32(const PairSetup& st, const SensorDev& S, V3 d, float& t, float& t_err) {
+    V3 m0 = {st.m[0], st.m[1], st.m[2]}, m1 = {st.m[3], st.m[4], st.m[5]}, m2 = {st.m[6], st.m[7], st.m[8]};
+    float E0 = vdot(d, m0), E1 = vdot(d, m1), E2 = vdot(d, m2);
+    float dn = vdot(d, {st.n[0], st.n[1], st.n[2]});
+    t = __fdiv_rn(st.det, dn);
+    t_err = 0.f;
+    if (!RECHECK) {
+        if (E0 < 0.f || E1 < 0.f || E2 < 0.f) return T_MISS;
+        if (!(t > 0.f) || !(t <= S.d_max) || t < S.d_min) return T_MISS;
+        return T_HIT;
+    }
+    bool unc_pair = st.state & 1u;
+    if (E0 < -st.tau[0] || E1 < -st.tau[1] || E2 < -st.tau[2]) {
+        if (!unc_pair) return T_MISS;
+        // orientation unknown: the other orientation may still hold
+        if (E0 <= st.tau[0] && E1 <= st.tau[1] && E2 <= st.tau[2]) {
+            t_err = 1.f;
+            return T_UNCERTAIN;
+        }
+        return T_MISS;
+    }
+    bool inside = E0 > st.tau[0] && E1 > st.tau[1] && E2 > st.tau[2];
+    float adn = fabsf(dn);
+    t_err = st.err_det + (fabsf(d.x) * st.G[0] + fabsf(d.y) * st.G[1] + fabsf(d.z) * st.G[2]) / adn;
+    if (!(t > 0.f) || !(t_err < 0.25f)) {
+        t_err = 1.f;
+        return (inside && !unc_pair && !(t > 0.f)) ? T_MISS : T_UNCERTAIN;
+    }
+    if (S.has_range) {
+        float lo = t * (1.f - t_err), hi = t * (1.f + t_err);
+        if (hi < S.d_min || lo > S.d_max) return T_MISS;
+        if (lo < S.d_min || hi > S.d_max) return T_UNCERTAIN;
+    }
+    if (!inside || unc_pair || t_err > TAU_T) return T_UNCERTAIN;
+    return T_HIT;
+}
+
+// ---------------------------------------------------------------------------
+// closest-hit commit, flags and the re-test queue
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void flag_ray(const CastArgs& a, uint32_t g) {
+    uint32_t bit = 1u << (g & 31u);
+    uint32_t old = atomicOr(&a.flag_bits[g >> 5], bit);
+    if (!(old & bit)) {
+        uint32_t idx = atomicAdd(&a.qcount[Q_FLAG], 1u);
+        if (idx < a.flag_cap)
+            a.flag_list[idx] = g;
+        else
+            atomicOr(a.error, (uint32_t)ERR_FLAG_CAP);
+    }
+}
+
+__device__ __forceinline__ void push_recheck(const CastArgs& a, uint32_t g, uint32_t tri) {
+    uint32_t idx = atomicAdd(&a.qcount[Q_RECHECK], 1u);
+    if (idx < a.recheck_cap)
+        a.recheck[idx] = make_uint2(g, tri);
+    else
+        atomicOr(a.error, (uint32_t)ERR_RECHECK_CAP);
+}
+
+__device__ __forceinline__ void dump_candidate(const CastArgs& a, uint32_t g, uint32_t tri) {
+    uint32_t idx = atomicAdd(a.dump_count, 1u);
+    if (idx < a.dump_cap) {
+        a.dump[2 * idx] = g;
+        a.dump[2 * idx + 1] = tri;
+    } else {
+        atomicOr(a.error, (uint32_t)ERR_DUMP_CAP);
+    }
+}
+
+// returns 1 if a hit was committed (for the statistics)
+template <bool RECHECK>
+__device__ __forceinline__ int commit(const CastArgs& a, uint32_t g, uint32_t tri, int res, float t, float t_err,
+                                      uint32_t& n_unc, uint32_t& n_ties) {
+    if (res == T_MISS) return 0;
+    unsigned long long* kp = &a.keys[g];
+    unsigned long long cur = __ldcg(kp);
+    float tcur = __uint_as_float((uint32_t)(cur >> 32));
+    if (res == T_UNCERTAIN) {
+        // a re-test can only change the result if it may beat the current best
+        if (t_err < 0.25f && t > 0.f && t * (1.f - t_err) > tcur * (1.f + BETA)) return 0;
+        flag_ray(a, g);
+        push_recheck(a, g, tri);
+        n_unc++;
+        return 0;
+    }
+    unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | tri;
+    if (!RECHECK) {
+        if (key < cur) atomicMin(kp, key);
+        return 1;
+    }
+    if (t > tcur * (1.f + BETA)) return 1;
+    unsigned long long old = atomicMin(kp, key);
+    uint32_t oid = (uint32_t)old;
+    if (oid != NO_HIT && oid != tri) {
+        float told = __uint_as_float((uint32_t)(old >> 32));
+        if (fabsf(t - told) <= BETA * fmaxf(t, told)) {
+            flag_ray(a, g);
+            push_recheck(a, g, tri);
+            push_recheck(a, g, oid);
+            n_ties++;
+        }
+    }
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// spans
+// ---------------------------------------------------------------------------
+struct Span {
+    int j_lo, j_hi;
+    int u_lo, n_r;  // ray span: unwrapped first ray and count
+    float a0;       // ray-unit coordinate of vertex 0's azimuth (normalised)
+    bool pierced;
+};
+
+// elevation extremum inside edge a->b (see Sec. 3.5.2 for the cone/edge
+// quadratic; here: the extreme elevation of the great-circle arc of the edge)
+__device__ __forceinline__ void edge_elev_extremum(V3 a, V3 b, float& smin, float& smax) {
+    V3 e = {b.x - a.x, b.y - a.y, b.z - a.z};
+    float ae = a.x * e.x + a.y * e.y + a.z * e.z;
+    float aa = a.x * a.x + a.y * a.y + a.z * a.z;
+    float ee = e.x * e.x + e.y * e.y + e.z * e.z;
+    float num = a.z * ae - e.z * aa;
+    float den = e.z * ae - a.z * ee;
+    if (!(fabsf(den) > 0.f)) return;
+    float lam = num / den;
+    if (!(lam > -1e-3f && lam < 1.001f)) return;
+    V3 m = {a.y * e.z - a.z * e.y, a.z * e.x - a.x * e.z, a.x * e.y - a.y * e.x};
+    float mm = m.x * m.x + m.y * m.y + m.z * m.z;
+    if (!(mm > 1e-12f * aa * ee)) return;  // edge collinear with the origin: vertices bound it
+    float v = sqrtf((m.x * m.x + m.y * m.y) / mm);
+    float qz = a.z + fminf(fmaxf(lam, 0.f), 1.f) * e.z;
+    float tol = 1e-4f * sqrtf(aa + ee);
+    if (qz >= -tol) smax = fmaxf(smax, v);
+    if (qz <= tol) smin = fminf(smin, -v);
+}
+
+__device__ __forceinline__ int lower_bound_sin(const float2* ch, int n, float x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (ch[mid].x < x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ int upper_bound_sin(const float2* ch, int n, float x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (ch[mid].x <= x)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// ray-unit coordinate of an absolute azimuth, normalised into one period
+__device__ __forceinline__ float ray_units(const SensorDev& S, float theta) {
+    float x = (theta - S.theta0) * S.inv_dtheta;
+    if (S.full) {
+        float n = (float)S.n_rays;
+        x -= n * floorf(x / n);
+    } else {
+        float g0 = -0.5f * (S.period - (float)S.n_rays);
+        x -= S.period * floorf((x - g0) / S.period);
+    }
+    return x;
+}
+
+// integer rays in [A, B] (ray units, around the normalised a0); wrap for
+// full circles, clip to the field of view otherwise
+__device__ __forceinline__ bool ray_interval(const SensorDev& S, float A, float B, int& u_lo, int& n_r) {
+    int n = (int)S.n_rays;
+    if (S.full) {
+        int ia = (int)ceilf(A), ib = (int)floorf(B);
+        if (ib < ia) return false;
+        int cnt = ib - ia + 1;
+        if (cnt >= n) {
+            u_lo = 0;
+            n_r = n;
+        } else {
+            u_lo = ia;
+            n_r = cnt;
+        }
+        return true;
+    }
+    int lo = n, hi = -1;
+    float P = S.period;
+#pragma unroll
+    for (int s = -1; s <= 1; ++s) {
+        int ia = (int)ceilf(A + s * P), ib = (int)floorf(B + s * P);
+        ia = max(ia, 0);
+        ib = min(ib, n - 1);
+        if (ia <= ib) {
+            lo = min(lo, ia);
+            hi = max(hi, ib);
+        }
+    }
+    if (hi < lo) return false;
+    u_lo = lo;
+    n_r = hi - lo + 1;
+    return true;
+}
+
+__device__ __forceinline__ float az_pad(V3 p) {
+    float h = sqrtf(p.x * p.x + p.y * p.y);
+    float r = sqrtf(p.x * p.x + p.y * p.y + p.z * p.z);
+    return h > 0.f ? 16.f * U32 * r / h : 10.f;
+}
+
+// Channel span (exact elevation extent, padded) and azimuth span (vertex
+// projections, Sec. 3.7; full circle when the vertical axis pierces the
+// triangle, which the paper covers with its all-CW / seam logic).
+__device__ __forceinline__ bool pair_span(const SensorDev& S, const float2* ch, const V3 p[3], float s_v[3], Span& sp) {
+    float smin = 2.f, smax = -2.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float r = sqrtf(p[k].x * p[k].x + p[k].y * p[k].y + p[k].z * p[k].z);
+        s_v[k] = r > 0.f ? p[k].z / r : 0.f;
+        smin = fminf(smin, s_v[k]);
+        smax = fmaxf(smax, s_v[k]);
+    }
+    edge_elev_extremum(p[0], p[1], smin, smax);
+    edge_elev_extremum(p[1], p[2], smin, smax);
+    edge_elev_extremum(p[2], p[0], smin, smax);
+    // does the vertical axis through the origin meet the triangle?
+    float c0 = cross2(p[0], p[1]), c1 = cross2(p[1], p[2]), c2 = cross2(p[2], p[0]);
+    float h0 = sqrtf(p[0].x * p[0].x + p[0].y * p[0].y), h1 = sqrtf(p[1].x * p[1].x + p[1].y * p[1].y),
+          h2 = sqrtf(p[2].x * p[2].x + p[2].y * p[2].y);
+    float t0 = 1e-5f * h0 * h1, t1 = 1e-5f * h1 * h2, t2 = 1e-5f * h2 * h0;
+    bool pierced = (c0 >= -t0 && c1 >= -t1 && c2 >= -t2) || (c0 <= t0 && c1 <= t1 && c2 <= t2);
+    if (pierced) {
+        if (fmaxf(p[0].z, fmaxf(p[1].z, p[2].z)) > 0.f) smax = 1.f;
+        if (fminf(p[0].z, fminf(p[1].z, p[2].z)) < 0.f) smin = -1.f;
+    }
+    int n_ch = (int)S.n_ch;
+    int jl = lower_bound_sin(ch, n_ch, smin - EPS_S);
+    int jh = upper_bound_sin(ch, n_ch, smax + EPS_S) - 1;
+    if (jl > jh) return false;
+    sp.j_lo = jl;
+    sp.j_hi = jh;
+    sp.pierced = pierced;
+    float th0 = atan2f(p[0].y, p[0].x);
+    sp.a0 = ray_units(S, th0);
+    float A, B;
+    if (pierced) {
+        A = sp.a0 - 0.5f * S.period;
+        B = sp.a0 + 0.5f * S.period;
+        if (S.full) {
+            sp.u_lo = 0;
+            sp.n_r = (int)S.n_rays;
+            return true;
+        }
+    } else {
+        float d1 = atan2f(cross2(p[0], p[1]), dot2(p[0], p[1]));
+        float d2 = atan2f(cross2(p[0], p[2]), dot2(p[0], p[2]));
+        float pad = EPS_T + az_pad(p[0]) + az_pad(p[1]) + az_pad(p[2]);
+        float lo = fminf(0.f, fminf(d1, d2)) - pad, hi = fmaxf(0.f, fmaxf(d1, d2)) + pad;
+        if (hi - lo >= 6.2831f) {
+            A = sp.a0 - 0.5f * S.period;
+            B = sp.a0 + 0.5f * S.period;
+        } else {
+            A = sp.a0 + lo * S.inv_dtheta;
+            B = sp.a0 + hi * S.inv_dtheta;
+        }
+    }
+    return ray_interval(S, A - PADR, B + PADR, sp.u_lo, sp.n_r);
+}
+
+// closest-point distance from the origin to the triangle (w = vertices
+// relative to the origin), for the range cull (App. A.4.1 Step 1: delta_min)
+__device__ __forceinline__ float closest_dist(V3 a, V3 b, V3 c) {
+    V3 ab = {b.x - a.x, b.y - a.y, b.z - a.z}, ac = {c.x - a.x, c.y - a.y, c.z - a.z};
+    V3 ap = {-a.x, -a.y, -a.z};
+    float d1 = ab.x * ap.x + ab.y * ap.y + ab.z * ap.z, d2 = ac.x * ap.x + ac.y * ap.y + ac.z * ap.z;
+    if (d1 <= 0.f && d2 <= 0.f) return sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+    V3 bp = {-b.x, -b.y, -b.z};
+    float d3 = ab.x * bp.x + ab.y * bp.y + ab.z * bp.z, d4 = ac.x * bp.x + ac.y * bp.y + ac.z * bp.z;
+    if (d3 >= 0.f && d4 <= d3) return sqrtf(b.x * b.x + b.y * b.y + b.z * b.z);
+    float vc = d1 * d4 - d3 * d2;
+    if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
+        float v = d1 / (d1 - d3);
+        V3 q = {a.x + v * ab.x, a.y + v * ab.y, a.z + v * ab.z};
+        return sqrtf(q.x * q.x + q.y * q.y + q.z * q.z);
+    }
+    V3 cp = {-c.x, -c.y, -c.z};
+    float d5 = ab.x * cp.x + ab.y * cp.y + ab.z * cp.z, d6 = ac.x * cp.x + ac.y * cp.y + ac.z * cp.z;
+    if (d6 >= 0.f && d5 <= d6) return sqrtf(c.x * c.x + c.y * c.y + c.z * c.z);
+    float vb = d5 * d2 - d1 * d6;
+    if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
+        float w = d2 / (d2 - d6);
+        V3 q = {a.x + w * ac.x, a.y + w * ac.y, a.z + w * ac.z};
+        return sqrtf(q.x * q.x + q.y * q.y + q.z * q.z);
+    }
+    float va = d3 * d6 - d5 * d4;
+    if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
+        float w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+        V3 q = {b.x + w * (c.x - b.x), b.y + w * (c.y - b.y), b.z + w * (c.z - b.z)};
+        return sqrtf(q.x * q.x + q.y * q.y + q.z * q.z);
+    }
+    float den = 1.f / (va + vb + vc);
+    float v = vb * den, w = vc * den;
+    V3 q = {a.x + ab.x * v + ac.x * w, a.y + ab.y * v + ac.y * w, a.z + ab.z * v + ac.z * w};
+    return sqrtf(q.x * q.x + q.y * q.y + q.z * q.z);
+}
+
+// ---------------------------------------------------------------------------
+// k_init
+// ---------------------------------------------------------------------------
+__global__ void k_init(CastArgs a) {
+    uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (uint32_t g = tid; g < a.n_rays_total; g += stride) a.keys[g] = KEY_MISS;
+    uint32_t nw = (a.n_rays_total + 31u) >> 5;
+    for (uint32_t q = tid; q < nw; q += stride) a.flag_bits[q] = 0u;
+    if (tid < Q_NUM) a.qcount[tid] = 0u;
+    if (tid < C_NUM) a.counters[tid] = 0ull;
+    if (tid == 0) *a.error = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// k_cull: persistent over triangle blocks, all sensors of the cast per triangle
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void warp_add(unsigned long long* ctr, uint32_t v) {
+    uint32_t s = __reduce_add_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, (unsigned long long)s);
+}
+
+template <bool RECHECK, bool BRUTE>
+__global__ void __launch_bounds__(256) k_cull(CastArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    SensorDev* s_sens = reinterpret_cast<SensorDev*>(smem);
+    float2* s_ch = reinterpret_cast<float2*>(smem + sizeof(SensorDev) * a.n_sensors);
+    size_t off = sizeof(SensorDev) * a.n_sensors + sizeof(float2) * a.total_ch;
+    off = (off + 15) & ~size_t(15);
+    float* s_tri = reinterpret_cast<float*>(smem + off);
+
+    for (uint32_t q = threadIdx.x; q < a.n_sensors * (uint32_t)(sizeof(SensorDev) / 4); q += blockDim.x)
+        reinterpret_cast<uint32_t*>(s_sens)[q] = reinterpret_cast<const uint32_t*>(a.sensors)[q];
+    __syncthreads();
+    for (uint32_t sn = 0; sn < a.n_sensors; ++sn) {
+        const SensorDev& S = s_sens[sn];
+        for (uint32_t j = threadIdx.x; j < S.n_ch; j += blockDim.x) s_ch[S.ch_loc + j] = a.ch_sc[S.ch_off + j];
+    }
+
+    const bool cull_back = a.flags & 2u;
+    const bool dump = a.flags & 16u;
+    uint32_t c_live = 0, c_cand = 0, c_inl = 0, c_big = 0, c_tests = 0, c_hits = 0, c_unc = 0, c_ties = 0;
+
+    const uint32_t bsz = blockDim.x;
+    for (uint32_t base = blockIdx.x * bsz; base < a.n_tris; base += gridDim.x * bsz) {
+        __syncthreads();
+        uint32_t cnt = min(bsz, a.n_tris - base);
+        // triangles are 36 B; a block's slice starts 16-B aligned (bsz % 4 == 0)
+        const float4* src = reinterpret_cast<const float4*>(a.tris + 9ull * base);
+        uint32_t n4 = (cnt * 9u + 3u) >> 2;
+        for (uint32_t q = threadIdx.x; q < n4; q += bsz) reinterpret_cast<float4*>(s_tri)[q] = src[q];
+        __syncthreads();
+        if (threadIdx.x >= cnt) continue;
+        const uint32_t tri = base + threadIdx.x;
+        TriW T;
+        tri_world(s_tri + 9 * threadIdx.x, T);
+        if (T.n.x == 0.f && T.n.y == 0.f && T.n.z == 0.f) continue;  // zero area: never hit
+
+        for (uint32_t sn = 0; sn < a.n_sensors; ++sn) {
+            const SensorDev& S = s_sens[sn];
+            V3 w[3], p[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                w[k] = rel_origin(S, T.v[k]);
+                p[k] = rotB(S.B, w[k]);
+            }
+            float det = vdot(w[0], T.n);
+            float err_det = det_error(w[0], T);
+            bool det_unc = fabsf(det) <= err_det;
+            if (!RECHECK && det == 0.f) continue;        // origin in the plane: t = 0, never a hit
+            if (RECHECK && det == 0.f && !det_unc) continue;
+            if (cull_back && det > 0.f && (!RECHECK || !det_unc)) continue;   // facing <=> det < 0
+            if (!BRUTE && S.has_range) {
+                float dmin = closest_dist(w[0], w[1], w[2]);
+                float dmax = fmaxf(vnorm(w[0]), fmaxf(vnorm(w[1]), vnorm(w[2])));
+                if (dmin > S.d_max * (1.f + 1e-5f) + 1e-6f) continue;
+                if (dmax < S.d_min * (1.f - 1e-5f) - 1e-6f) continue;
+            }
+            Span sp;
+            float s_v[3];
+            if (BRUTE) {
+                sp.j_lo = 0;
+                sp.j_hi = (int)S.n_ch - 1;
+                sp.u_lo = 0;
+                sp.n_r = (int)S.n_rays;
+            } else if (!pair_span(S, s_ch + S.ch_loc, p, s_v, sp)) {
+                continue;
+            }
+            uint32_t ncand = (uint32_t)(sp.j_hi - sp.j_lo + 1) * (uint32_t)sp.n_r;
+            c_live++;
+            c_cand += ncand;
+            if (!BRUTE && ncand > a.inline_max) {
+                // deferred list append: one atomic per coalesced group (ballot + popc rank)
+                cg::coalesced_group grp = cg::coalesced_threads();
+                uint32_t b0 = 0;
+                if (grp.thread_rank() == 0) b0 = atomicAdd(&a.qcount[Q_BIG], grp.size());
+                b0 = grp.shfl(b0, 0) + grp.thread_rank();
+                if (b0 < a.big_cap) {
+                    BigPair bp;
+                    bp.tri = tri;
+                    bp.sensor = (uint16_t)sn;
+                    bp.flags = sp.pierced ? 1 : 0;
+                    bp.j_lo = (uint16_t)sp.j_lo;
+                    bp.j_hi = (uint16_t)sp.j_hi;
+                    bp.u_lo = sp.u_lo;
+                    bp.n_r = (uint32_t)sp.n_r;
+                    bp.a0 = sp.a0;
+                    bp.pad_[0] = bp.pad_[1] = 0;
+                    a.big[b0] = bp;
+                } else {
+                    atomicOr(a.error, (uint32_t)ERR_BIG_CAP);
+                }
+                c_big++;
+                continue;
+            }
+            c_inl += ncand;
+            PairSetup st;
+            make_setup(S, T, w, p, det, err_det, st);
+            const float2* chs = s_ch + S.ch_loc;
+            const float2* azs = a.az_sc + S.az_off;
+            const int n = (int)S.n_rays;
+            int r0 = imod(sp.u_lo, n);
+            for (int j = sp.j_lo; j <= sp.j_hi; ++j) {
+                float2 chv = chs[j];
+                uint32_t gbase = S.ray_off + (uint32_t)j * (uint32_t)n;
+                int i = r0;
+                for (int q = 0; q < sp.n_r; ++q) {
+                    V3 d = ray_dir(chv, __ldg(&azs[i]));
+                    float t, terr;
+                    int res = test_fp32<RECHECK>(st, S, d, t, terr);
+                    c_tests++;
+                    if (dump) dump_candidate(a, gbase + i, tri);
+                    c_hits += commit<RECHECK>(a, gbase + i, tri, res, t, terr, c_unc, c_ties);
+                    if (++i == n) i = 0;
+                }
+            }
+        }
+    }
+    // statistics (all threads reach here)
+    warp_add(&a.counters[C_PAIRS_LIVE], c_live);
+    warp_add(&a.counters[C_CAND], c_cand);
+    warp_add(&a.counters[C_CAND_INLINE], c_inl);
+    warp_add(&a.counters[C_BIG], c_big);
+    warp_add(&a.counters[C_TESTS], c_tests);
+    warp_add(&a.counters[C_HITS], c_hits);
+    warp_add(&a.counters[C_UNCERTAIN], c_unc);
+    warp_add(&a.counters[C_TIES], c_ties);
+}
+
+// ---------------------------------------------------------------------------
+// per-channel azimuth span of a deferred pair (cone/plane crossings)
+// ---------------------------------------------------------------------------
+// Relative azimuth (to vertex 0) of every crossing of channel level s (sin)
+// with the triangle's edges: the quadratic of Sec. 3.5.2
+// (a_z + l e_z)^2 c^2 - s^2 |a_h + l e_h|^2 = 0 on the forward nappe, or the
+// plane case of Sec. 3.5.1 for s == 0.  Returns false if no edge crosses.
+__device__ __forceinline__ bool channel_span_rel(const V3 p[3], const float s_v[3], float s, float c, float& lo,
+                                                 float& hi) {
+    bool any = false;
+    lo = 1e30f;
+    hi = -1e30f;
+    V3 p0 = p[0];
+    auto include = [&](V3 q, float extra) {
+        float ang = atan2f(cross2(p0, q), dot2(p0, q));
+        float pad = EPS_ROW + az_pad(q) + extra;
+        lo = fminf(lo, ang - pad);
+        hi = fmaxf(hi, ang + pad);
+        any = true;
+    };
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        V3 a = p[k], b = p[k == 2 ? 0 : k + 1];
+        float emin = fminf(s_v[k], s_v[k == 2 ? 0 : k + 1]), emax = fmaxf(s_v[k], s_v[k == 2 ? 0 : k + 1]);
+        edge_elev_extremum(a, b, emin, emax);
+        if (s < emin - EPS_S || s > emax + EPS_S) continue;
+        V3 e = {b.x - a.x, b.y - a.y, b.z - a.z};
+        bool found = false;
+        if (s == 0.f) {
+            if (a.z == 0.f && b.z == 0.f) {
+                include(a, 0.f);
+                include(b, 0.f);
+                found = true;
+            } else if ((a.z <= 0.f && b.z >= 0.f) || (a.z >= 0.f && b.z <= 0.f)) {
+                float lam = a.z / (a.z - b.z);
+                V3 q = {a.x + lam * e.x, a.y + lam * e.y, a.z + lam * e.z};
+                include(q, 0.f);
+                found = true;
+            }
+        } else {
+            float c2 = c * c, s2 = s * s;
+            float A = e.z * e.z * c2 - s2 * (e.x * e.x + e.y * e.y);
+            float Bh = a.z * e.z * c2 - s2 * (a.x * e.x + a.y * e.y);
+            float C = a.z * a.z * c2 - s2 * (a.x * a.x + a.y * a.y);
+            float lam[2];
+            int nl = 0;
+            float scaleA = e.z * e.z * c2 + s2 * (e.x * e.x + e.y * e.y);
+            if (fabsf(A) <= 1e-5f * scaleA) {
+                if (Bh != 0.f) lam[nl++] = -C / (2.f * Bh);
+            } else {
+                float disc = Bh * Bh - A * C;
+                if (disc >= 0.f) {
+                    float sq = sqrtf(disc);
+                    float qq = -(Bh + copysignf(sq, Bh));
+                    lam[nl++] = qq / A;
+                    if (qq != 0.f) lam[nl++] = C / qq;
+                } else if (disc > -1e-3f * Bh * Bh) {
+                    lam[nl++] = -Bh / A;  // tangent touch
+                }
+            }
+            for (int r = 0; r < nl; ++r) {
+                float l = lam[r];
+                if (!(l >= -1e-4f && l <= 1.0001f)) continue;
+                l = fminf(fmaxf(l, 0.f), 1.f);
+                V3 q = {a.x + l * e.x, a.y + l * e.y, a.z + l * e.z};
+                float qr = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z);
+                if ((s > 0.f && q.z < -1e-5f * qr) || (s < 0.f && q.z > 1e-5f * qr)) continue;  // mirror nappe
+                include(q, 0.f);
+                found = true;
+            }
+        }
+        if (!found) {  // numerics gave no usable root although the edge spans the level
+            include(a, 0.f);
+            include(b, 0.f);
+        }
+    }
+    return any;
+}
+
+__global__ void __launch_bounds__(256) k_expand(CastArgs a) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t n_big = min(*(volatile uint32_t*)&a.qcount[Q_BIG], a.big_cap);
+    const uint32_t CH = a.chunk_rays;
+    for (uint32_t bp = gw; bp < n_big; bp += nw) {
+        BigPair P = a.big[bp];
+        const SensorDev& S = a.sensors[P.sensor];
+        TriW T;
+        float t9[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) t9[q] = __ldg(&a.tris[9ull * P.tri + q]);
+        tri_world(t9, T);
+        V3 w[3], p[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            w[k] = rel_origin(S, T.v[k]);
+            p[k] = rotB(S.B, w[k]);
+        }
+        float det = vdot(w[0], T.n);
+        float err_det = det_error(w[0], T);
+        if (lane == 0) {
+            PairSetup st;
+            make_setup(S, T, w, p, det, err_det, st);
+            a.setups[bp] = st;
+        }
+        float s_v[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float r = sqrtf(p[k].x * p[k].x + p[k].y * p[k].y + p[k].z * p[k].z);
+            s_v[k] = r > 0.f ? p[k].z / r : 0.f;
+        }
+        const int n = (int)S.n_rays;
+        const bool full_pair = P.n_r >= (uint32_t)n;
+        for (int jb = P.j_lo; jb <= (int)P.j_hi; jb += 32) {
+            int j = jb + (int)lane;
+            uint32_t nch = 0;
+            int r_first = 0, cnt = 0;
+            if (j <= (int)P.j_hi) {
+                int u_lo = P.u_lo, n_r = (int)P.n_r;
+                if (!(P.flags & 1u)) {
+                    float2 sc = a.ch_sc[S.ch_off + j];
+                    float lo, hi;
+                    if (channel_span_rel(p, s_v, sc.x, sc.y, lo, hi)) {
+                        int ru, rn;
+                        if (hi - lo < 6.2831f &&
+                            ray_interval(S, P.a0 + lo * S.inv_dtheta - PADR, P.a0 + hi * S.inv_dtheta + PADR, ru, rn)) {
+                            if (full_pair) {
+                                u_lo = ru;
+                                n_r = rn;
+                            } else {
+                                int l2 = max(ru, u_lo), h2 = min(ru + rn - 1, u_lo + n_r - 1);
+                                u_lo = l2;
+                                n_r = h2 - l2 + 1;
+                            }
+                        } else if (!(hi - lo < 6.2831f)) {
+                            // keep the pair span
+                        } else {
+                            n_r = 0;
+                        }
+                    } else {
+                        n_r = 0;
+                    }
+                }
+                if (n_r > 0) {
+                    cnt = n_r;
+                    r_first = imod(u_lo, n);
+                    nch = (uint32_t)((cnt + (int)CH - 1) / (int)CH);
+                }
+            }
+            // warp prefix sum of chunk counts -> one atomic per warp
+            uint32_t incl = nch;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)lane >= o) incl += v;
+            }
+            uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            if (total == 0) continue;
+            uint32_t b0 = 0;
+            if (lane == 0) b0 = atomicAdd(&a.qcount[Q_CHUNK], total);
+            b0 = __shfl_sync(0xffffffffu, b0, 0) + incl - nch;
+            for (uint32_t q = 0; q < nch; ++q) {
+                uint32_t idx = b0 + q;
+                if (idx < a.chunk_cap) {
+                    int r = r_first + (int)(q * CH);
+                    if (r >= n) r -= n;
+                    a.chunks[idx] = make_uint4(bp, (uint32_t)j, (uint32_t)r, (uint32_t)min((int)CH, cnt - (int)(q * CH)));
+                } else {
+                    atomicOr(a.error, (uint32_t)ERR_CHUNK_CAP);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_test: one warp per chunk of one (pair, channel) row
+// ---------------------------------------------------------------------------
+template <bool RECHECK>
+__global__ void __launch_bounds__(256) k_test(CastArgs a) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t n_chunks = min(*(volatile uint32_t*)&a.qcount[Q_CHUNK], a.chunk_cap);
+    const bool dump = a.flags & 16u;
+    uint32_t c_tests = 0, c_hits = 0, c_unc = 0, c_ties = 0;
+    for (uint32_t c = gw; c < n_chunks; c += nw) {
+        uint4 ck = a.chunks[c];
+        const uint32_t bp = ck.x, j = ck.y, r0 = ck.z, cnt = ck.w;
+        const uint32_t tri = a.big[bp].tri;
+        const SensorDev& S = a.sensors[a.big[bp].sensor];
+        const PairSetup st = a.setups[bp];
+        const uint32_t n = S.n_rays;
+        const float2 chv = a.ch_sc[S.ch_off + j];
+        const uint32_t gbase = S.ray_off + j * n;
+        for (uint32_t q = lane; q < cnt; q += 32) {
+            uint32_t i = r0 + q;
+            if (i >= n) i -= n;
+            V3 d = ray_dir(chv, __ldg(&a.az_sc[S.az_off + i]));
+            float t, terr;
+            int res = test_fp32<RECHECK>(st, S, d, t, terr);
+            c_tests++;
+            if (dump) dump_candidate(a, gbase + i, tri);
+            c_hits += commit<RECHECK>(a, gbase + i, tri, res, t, terr, c_unc, c_ties);
+        }
+    }
+    warp_add(&a.counters[C_TESTS], c_tests);
+    warp_add(&a.counters[C_HITS], c_hits);
+    warp_add(&a.counters[C_UNCERTAIN], c_unc);
+    warp_add(&a.counters[C_TIES], c_ties);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.counters[C_CHUNKS] = n_chunks;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 re-test (world frame, same watertight edge-function formulation)
+// ---------------------------------------------------------------------------
+struct D3 {
+    double x, y, z;
+};
+__device__ __forceinline__ D3 dsub(D3 a, D3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ double ddot(D3 a, D3 b) { return __fma_rn(a.x, b.x, __fma_rn(a.y, b.y, __dmul_rn(a.z, b.z))); }
+__device__ __forceinline__ D3 dcross(D3 a, D3 b) {
+    return {__dsub_rn(__dmul_rn(a.y, b.z), __dmul_rn(a.z, b.y)), __dsub_rn(__dmul_rn(a.z, b.x), __dmul_rn(a.x, b.z)),
+            __dsub_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x))};
+}
+
+__device__ __forceinline__ void decode_ray(const CastArgs& a, uint32_t g, uint32_t& sn, uint32_t& j, uint32_t& i) {
+    sn = 0;
+    for (uint32_t k = 1; k < a.n_sensors; ++k)
+        if (a.sensors[k].ray_off <= g) sn = k;
+    const SensorDev& S = a.sensors[sn];
+    uint32_t loc = g - S.ray_off;
+    j = loc / S.n_rays;
+    i = loc - j * S.n_rays;
+}
+
+// returns the u64 key of the FP64 result (KEY_MISS on a miss)
+__device__ unsigned long long test_fp64(const CastArgs& a, uint32_t g, uint32_t tri) {
+    uint32_t sn, j, i;
+    decode_ray(a, g, sn, j, i);
+    const SensorDev& S = a.sensors[sn];
+    double2 ch = a.ch_sc64[S.ch_off + j];
+    double2 az = a.az_sc64[S.az_off + i];
+    double ca = az.y * ch.y, sa = az.x * ch.y, su = ch.x;
+    D3 d = {ca * S.B64[0] + sa * S.B64[3] + su * S.B64[6], ca * S.B64[1] + sa * S.B64[4] + su * S.B64[7],
+            ca * S.B64[2] + sa * S.B64[5] + su * S.B64[8]};
+    const float* t9 = a.tris + 9ull * tri;
+    V3 vf[3];
+    D3 v[3], w[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        vf[k] = {t9[3 * k], t9[3 * k + 1], t9[3 * k + 2]};
+        v[k] = {(double)vf[k].x, (double)vf[k].y, (double)vf[k].z};
+        w[k] = {v[k].x - S.o64[0], v[k].y - S.o64[1], v[k].z - S.o64[2]};
+    }
+    D3 n = dcross(dsub(v[1], v[0]), dsub(v[2], v[0]));
+    if (n.x == 0.0 && n.y == 0.0 && n.z == 0.0) return KEY_MISS;
+    double det = ddot(w[0], n);
+    if (det == 0.0) return KEY_MISS;
+    if ((a.flags & 2u) && det > 0.0) return KEY_MISS;  // back-facing
+    double fold = det < 0.0 ? -1.0 : 1.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int k1 = k == 2 ? 0 : k + 1;
+        bool fwd = !lex_less(vf[k1], vf[k]);
+        int b = fwd ? k : k1, o = fwd ? k1 : k;
+        D3 m = dcross(w[b], dsub(v[o], v[b]));
+        double E = ddot(d, m) * (fwd ? fold : -fold);
+        if (E < 0.0) return KEY_MISS;
+    }
+    double dn = ddot(d, n);
+    if (dn == 0.0) return KEY_MISS;
+    double t = det / dn;
+    if (!(t > 0.0) || t < S.d_min64 || t > S.d_max64) return KEY_MISS;
+    float tf = __double2float_rn(t);
+    return ((unsigned long long)__float_as_uint(tf) << 32) | tri;
+}
+
+// R1: every flagged ray starts from the FP64 result of its FP32 winner
+__global__ void k_recheck_rays(CastArgs a) {
+    uint32_t nf = min(*(volatile uint32_t*)&a.qcount[Q_FLAG], a.flag_cap);
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nf; q += gridDim.x * blockDim.x) {
+        uint32_t g = a.flag_list[q];
+        unsigned long long k = a.keys[g];
+        uint32_t id = (uint32_t)k;
+        a.keys64[g] = id == NO_HIT ? KEY_MISS : test_fp64(a, g, id);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_FLAGGED] = nf;
+}
+
+// R2: FP64 re-test of every queued (ray, triangle) pair
+__global__ void k_recheck_pairs(CastArgs a) {
+    uint32_t np = min(*(volatile uint32_t*)&a.qcount[Q_RECHECK], a.recheck_cap);
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
+        uint2 pr = a.recheck[q];
+        unsigned long long k = test_fp64(a, pr.x, pr.y);
+        if (k != KEY_MISS) atomicMin(&a.keys64[pr.x], k);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_RECHECK] = np;
+}
+
+// R3 fused into decode: flagged rays take the FP64 key
+__global__ void k_decode(CastArgs a, int recheck) {
+    uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_rays_total; g += stride) {
+        unsigned long long k = a.keys[g];
+        if (recheck && (a.flag_bits[g >> 5] >> (g & 31u) & 1u)) k = a.keys64[g];
+        a.out_dist[g] = __uint_as_float((uint32_t)(k >> 32));
+        a.out_tri[g] = (uint32_t)k;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_PAIRS] = (unsigned long long)a.n_tris * a.n_sensors;
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+size_t cull_smem_bytes(const CastArgs& a, const LaunchCfg& cfg) {
+    size_t off = sizeof(SensorDev) * a.n_sensors + sizeof(float2) * a.total_ch;
+    off = (off + 15) & ~size_t(15);
+    return off + sizeof(float) * 9 * (size_t)cfg.cull_block + 16;
+}
+
+template <bool R, bool B>
+static void set_cull_attr(size_t smem) {
+    static size_t done = 0;
+    if (smem > 48 * 1024 && smem > done) {
+        cudaFuncSetAttribute(k_cull<R, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        done = smem;
+    }
+}
+
+const char* const kKernelNames[K_NUM] = {"k_init", "k_cull", "k_expand", "k_test",
+                                          "k_recheck_rays", "k_recheck_pairs", "k_decode"};
+
+int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t st, const KernelMarks* marks) {
+    const bool recheck = a.flags & 1u;
+    const bool brute = a.flags & 4u;
+    int launches = 0;
+    auto mark = [&](int k, int phase) {
+        if (marks && marks->fn) marks->fn(marks->user, k, phase, st);
+    };
+    int init_blocks = (int)std::min<uint32_t>((a.n_rays_total + 255) / 256, (uint32_t)n_sm * 8);
+    mark(K_INIT, 0);
+    k_init<<<max(init_blocks, 1), 256, 0, st>>>(a);
+    mark(K_INIT, 1);
+    launches++;
+    size_t smem = cull_smem_bytes(a, cfg);
+    uint32_t max_blocks = (a.n_tris + cfg.cull_block - 1) / cfg.cull_block;
+    int cull_grid = (int)std::min<uint32_t>(max_blocks, (uint32_t)(n_sm * cfg.cull_blocks_per_sm));
+    if (cull_grid < 1) cull_grid = 1;
+    mark(K_CULL, 0);
+    if (recheck && brute) {
+        set_cull_attr<true, true>(smem);
+        k_cull<true, true><<<cull_grid, cfg.cull_block, smem, st>>>(a);
+    } else if (recheck) {
+        set_cull_attr<true, false>(smem);
+        k_cull<true, false><<<cull_grid, cfg.cull_block, smem, st>>>(a);
+    } else if (brute) {
+        set_cull_attr<false, true>(smem);
+        k_cull<false, true><<<cull_grid, cfg.cull_block, smem, st>>>(a);
+    } else {
+        set_cull_attr<false, false>(smem);
+        k_cull<false, false><<<cull_grid, cfg.cull_block, smem, st>>>(a);
+    }
+    mark(K_CULL, 1);
+    launches++;
+    if (!brute) {
+        mark(K_EXPAND, 0);
+        k_expand<<<n_sm * 8, 256, 0, st>>>(a);
+        mark(K_EXPAND, 1);
+        mark(K_TEST, 0);
+        if (recheck)
+            k_test<true><<<n_sm * 8, cfg.test_block, 0, st>>>(a);
+        else
+            k_test<false><<<n_sm * 8, cfg.test_block, 0, st>>>(a);
+        mark(K_TEST, 1);
+        launches += 2;
+    }
+    if (recheck) {
+        mark(K_RECHECK_RAYS, 0);
+        k_recheck_rays<<<n_sm * 2, 256, 0, st>>>(a);
+        mark(K_RECHECK_RAYS, 1);
+        mark(K_RECHECK_PAIRS, 0);
+        k_recheck_pairs<<<n_sm * 2, 256, 0, st>>>(a);
+        mark(K_RECHECK_PAIRS, 1);
+        launches += 2;
+    }
+    int dec_blocks = (int)std::min<uint32_t>((a.n_rays_total + 255) / 256, (uint32_t)n_sm * 8);
+    mark(K_DECODE, 0);
+    k_decode<<<max(dec_blocks, 1), 256, 0, st>>>(a, recheck ? 1 : 0);
+    mark(K_DECODE, 1);
+    launches++;
+    return launches;
+}
+
+}  // namespace grca

@@ -142,48 +142,39 @@ def grid_mesh(x0, x1, y0, y1, nx, ny, z=0.0) -> Mesh:
 
 def box_mesh(size, n=1) -> Mesh:
     """Closed box centred at 0 with sides `size`, each face split into n x n quads.
-    Lattice points are shared between faces (one vertex per lattice point)."""
+    Lattice points are shared between faces (one vertex per surface lattice point)."""
     n = max(1, int(n))
     sx, sy, sz = (float(s) for s in size)
-    # lattice coordinates 0..n on each axis; surface points only
-    idx = {}
-    verts = []
-
-    def vid(i, j, k):
-        key = (i, j, k)
-        v = idx.get(key)
-        if v is None:
-            v = len(verts)
-            idx[key] = v
-            verts.append((sx * (i / n - 0.5), sy * (j / n - 0.5), sz * (k / n - 0.5)))
-        return v
-
+    L = n + 1
+    surf = np.zeros((L, L, L), dtype=bool)
+    surf[[0, -1], :, :] = True
+    surf[:, [0, -1], :] = True
+    surf[:, :, [0, -1]] = True
+    pts = np.argwhere(surf)
+    idx = -np.ones((L, L, L), dtype=np.int64)
+    idx[surf] = np.arange(pts.shape[0])
+    verts = np.stack([sx * (pts[:, 0] / n - 0.5), sy * (pts[:, 1] / n - 0.5), sz * (pts[:, 2] / n - 0.5)], 1)
+    pg, qg = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    pg, qg = pg.ravel(), qg.ravel()
     faces = []
-
-    def face(fix_axis, fix_val, outward):
-        ax = [a for a in range(3) if a != fix_axis]
-        for p in range(n):
-            for q in range(n):
-                def L(a_, b_):
-                    c = [0, 0, 0]
-                    c[fix_axis] = fix_val
-                    c[ax[0]] = a_
-                    c[ax[1]] = b_
-                    return vid(*c)
-                v00, v10, v11, v01 = L(p, q), L(p + 1, q), L(p + 1, q + 1), L(p, q + 1)
-                # orientation: (ax0 x ax1) points along +fix_axis for even permutations
-                e = np.zeros(3); e[ax[0]] = 1
-                g = np.zeros(3); g[ax[1]] = 1
-                sgn = np.cross(e, g)[fix_axis]
-                if (sgn > 0) == outward:
-                    faces.append((v00, v10, v11)); faces.append((v00, v11, v01))
-                else:
-                    faces.append((v00, v11, v10)); faces.append((v00, v01, v11))
-
-    for a in range(3):
-        face(a, 0, False)
-        face(a, n, True)
-    return Mesh(np.array(verts, dtype=np.float64), np.array(faces, dtype=np.int64))
+    for axis in range(3):
+        ax = [a for a in range(3) if a != axis]
+        e = np.zeros(3); e[ax[0]] = 1
+        g = np.zeros(3); g[ax[1]] = 1
+        sgn = np.cross(e, g)[axis]
+        for side, outward in ((0, False), (n, True)):
+            def lat(a_, b_):
+                c = [None, None, None]
+                c[axis] = np.full_like(a_, side)
+                c[ax[0]] = a_
+                c[ax[1]] = b_
+                return idx[c[0], c[1], c[2]]
+            v00, v10, v11, v01 = lat(pg, qg), lat(pg + 1, qg), lat(pg + 1, qg + 1), lat(pg, qg + 1)
+            if (sgn > 0) == outward:
+                faces += [np.stack([v00, v10, v11], 1), np.stack([v00, v11, v01], 1)]
+            else:
+                faces += [np.stack([v00, v11, v10], 1), np.stack([v00, v01, v11], 1)]
+    return Mesh(verts.astype(np.float64), np.concatenate(faces, 0).astype(np.int64))
 
 
 def ellipsoid_mesh(radii, n_slices, n_stacks) -> Mesh:
@@ -535,7 +526,7 @@ def scene_c4(seed: int = 4, d_max=math.inf, mini: bool = False) -> Scene:
             s.dtheta *= 4
             s.theta0 = -math.pi if abs(s.n_rays * s.dtheta - 2 * math.pi) < 1e-9 else -(s.n_rays // 2) * s.dtheta
         return _big_scene("c4m", sens, seed, 1, 140, 30, 3500, 12, 5000, 6, 5000)
-    return _big_scene("c4", sens, seed, 1, 1000, 3150, 3500, 1200, 5000, 600, 5000)
+    return _big_scene("c4", sens, seed, 1, 1000, 3400, 3500, 1200, 5000, 600, 5000)
 
 
 def stress_set(sensors: List[Sensor], rng, n_items: int):
@@ -629,7 +620,7 @@ def scene_c5(seed: int = 5, mini: bool = False, n_stress: int = 1500) -> Scene:
             s.dtheta *= 4
         sc = _big_scene("c5m", sens, seed, 1, 140, 30, 3500, 12, 5000, 6, 5000, n_frames=60)
     else:
-        sc = _big_scene("c5", sens, seed, 1, 1000, 3150, 3500, 1200, 5000, 600, 5000, n_frames=60)
+        sc = _big_scene("c5", sens, seed, 1, 1000, 3400, 3500, 1200, 5000, 600, 5000, n_frames=60)
     rng = np.random.default_rng(seed + 1000)
     st, rays = stress_set(sens, rng, n_stress if not mini else max(30, n_stress // 50))
     sc.static_tris = np.ascontiguousarray(np.concatenate([sc.static_tris, st], 0))

@@ -1,0 +1,74 @@
+"""CPU tests of the boundary: libgrca.so builds for sm_103a, loads, and exports
+every function include/grca.h declares (no compute calls without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2605_10457_gb300 import build as B
+from paper_2605_10457_gb300 import grca
+
+HEADER = os.path.join(B.ROOT, "include", "grca.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(grca_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = B.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("grca_create_sensor", "grca_upload_triangles", "grca_update_vertices", "grca_cast"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_symbol():
+    assert sorted(grca.EXPORTS) == declared_functions()
+
+
+def test_status_strings(lib):
+    lib.grca_status_string.restype = ctypes.c_char_p
+    lib.grca_status_string.argtypes = [ctypes.c_int32]
+    assert lib.grca_status_string(0) == b"ok"
+    for code in (-1, -2, -3, -4, -5, -6):
+        s = lib.grca_status_string(code)
+        assert s and s != b"unknown status"
+    assert lib.grca_status_string(-99) == b"unknown status"
+
+
+def test_null_arguments_rejected_without_a_device(lib):
+    # argument checks run before any CUDA call
+    lib.grca_create.restype = ctypes.c_int32
+    lib.grca_create.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    assert lib.grca_create(None, 0, None) == -1
+    lib.grca_cast.restype = ctypes.c_int32
+    lib.grca_cast.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                                       ctypes.c_void_p]
+    assert lib.grca_cast(None, None, 0, None, None, 0, None) == -1
+    lib.grca_get_stats.restype = ctypes.c_int32
+    assert lib.grca_get_stats(None, None, None) == -1
+
+
+def test_struct_layouts_match_header():
+    # the ctypes mirrors must match the C layout (sizes computed by the C rules)
+    assert ctypes.sizeof(grca.grca_sensor_desc) == 12 * 8 + 8 + 4 + 4 + 4 * 8
+    assert ctypes.sizeof(grca.grca_options) == 3 * 8 + 4 * 4
+    assert ctypes.sizeof(grca.grca_stats) == 13 * 8 + 2 * 4
+
+
+def test_build_targets_sm103a_only():
+    # the build passes exactly one -gencode, for sm_103a
+    assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+All inputs are seeded synthetic scenes from `scenes`.  Small scenes are
+checked on every ray; larger ones on stratified ray samples the oracle can
+brute-force in seconds.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from grading import grade, stratified_rays
+from scenes import make_config, make_sensor, scene_c1, tiny_scene, Sensor
+
+pytestmark = pytest.mark.gpu
+
+
+def _caster(**opts):
+    from paper_2605_10457_gb300 import grca
+    return grca.Caster(0, **opts)
+
+
+def _cast(c, ids, flags):
+    import torch
+    d, t = c.cast(ids, flags)
+    torch.cuda.synchronize()
+    return d.cpu().numpy(), t.cpu().numpy().view(np.uint32)
+
+
+def _setup(scene, frame=0, **opts):
+    c = _caster(**opts)
+    ids = [c.add_sensor(s) for s in scene.sensors]
+    tris = scene.tris(frame)
+    c.upload(tris)
+    return c, ids, tris
+
+
+def _check(scene, tris, d, t, ray_ids=None, cull=False, fp32=False):
+    orc = oracle.Oracle(scene.sensors)
+    ref = oracle.cast(orc, tris, ray_ids, cull_backface=cull, ties=True)
+    rid = ref["ray_ids"]
+    g = grade(orc, tris, ref, d[rid], t[rid], edge_eps=(2e-6 if fp32 else 1e-7),
+              silhouette_eps=(2e-6 if fp32 else 1e-12), dist_rel=(1e-4 if fp32 else 1e-5))
+    return g
+
+
+# ---------------------------------------------------------------------------
+def test_c1_fp64_recheck_all_rays():
+    from paper_2605_10457_gb300.grca import CAST_FP64_RECHECK
+    sc = scene_c1()
+    c, ids, tris = _setup(sc)
+    d, t = _cast(c, ids, CAST_FP64_RECHECK)
+    st = c.stats()
+    assert st["device_error"] == 0
+    assert st["pairs"] == len(ids) * tris.shape[0]
+    g = _check(sc, tris, d, t)
+    assert g["errors"] == 0, g
+    assert g["hits"] > 3000
+
+
+def test_c1_plain_fp32_all_rays():
+    sc = scene_c1()
+    c, ids, tris = _setup(sc)
+    d, t = _cast(c, ids, 0)
+    g = _check(sc, tris, d, t, fp32=True)
+    assert g["errors"] <= 2, g   # FP32 only: reported, tolerance of the FP32 path
+
+
+@pytest.mark.parametrize("cfg", ["c1", "c2m", "c3m", "c4m"])
+def test_culling_never_drops_a_hit_brute_equals_culled(cfg):
+    """Plain FP32: the culled path and the no-cull brute force run the same
+    test on every pair, so any hit lost by a cull shows up as a difference."""
+    from paper_2605_10457_gb300.grca import CAST_BRUTE
+    sc = make_config(cfg)
+    c, ids, tris = _setup(sc)
+    if cfg in ("c3m", "c4m"):
+        ids = ids[:2]   # brute force is O(rays x tris); two sensors suffice here
+    d0, t0 = _cast(c, ids, 0)
+    d1, t1 = _cast(c, ids, CAST_BRUTE)
+    diff = np.nonzero((t0 != t1) | ~((d0 == d1) | (np.isinf(d0) & np.isinf(d1))))[0]
+    assert diff.size == 0, (diff[:10], t0[diff[:10]], t1[diff[:10]], d0[diff[:10]], d1[diff[:10]])
+
+
+def test_tiny_random_scenes_brute_equals_culled():
+    from paper_2605_10457_gb300.grca import CAST_BRUTE, CAST_FP64_RECHECK
+    for seed in range(6):
+        tris = tiny_scene(seed, n_tris=300, extent=6.0)
+        sens = [make_sensor((0.0, 0.0, 0.5), channels="c32", n_rays=720),
+                make_sensor((0.3, -0.2, 1.0), yaw=0.4, channels="c64", n_rays=512, fov_deg=180.0),
+                make_sensor((-0.5, 0.1, 0.2), yaw=-1.0, channels="uniform16", n_rays=360, pitch=0.3, roll=-0.2)]
+        c = _caster()
+        ids = [c.add_sensor(s) for s in sens]
+        c.upload(tris)
+        for fl in (0, CAST_FP64_RECHECK):
+            d0, t0 = _cast(c, ids, fl)
+            d1, t1 = _cast(c, ids, fl | CAST_BRUTE)
+            assert np.array_equal(t0, t1), (seed, fl, np.nonzero(t0 != t1)[0][:8])
+        sc = type("S", (), {"sensors": sens})
+        g = _check(sc, tris, d0, t0)
+        assert g["errors"] == 0, (seed, g)
+
+
+def test_candidate_spans_cover_every_exact_hit():
+    """Every (ray, triangle) pair that the FP64 oracle finds hitting must be
+    among the candidates the culling passes emit (debug dump)."""
+    import torch
+    from paper_2605_10457_gb300.grca import CAST_DUMP_CANDIDATES
+    sc = scene_c1()
+    c, ids, tris = _setup(sc)
+    cap = 8_000_000
+    pairs = torch.zeros(2 * cap, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    c.set_debug_dump(pairs, cnt)
+    _cast(c, ids, CAST_DUMP_CANDIDATES)
+    n = int(cnt.item())
+    assert 0 < n <= cap
+    got = pairs[:2 * n].view(-1, 2).cpu().numpy().astype(np.int64)
+    cand = set((got[:, 1] << 32 | got[:, 0]).tolist())
+    hits = oracle.triangle_hits(sc.sensors[0], tris)
+    need = (hits[:, 0] << 32) | hits[:, 1]
+    missing = [int(x) for x in need if int(x) not in cand]
+    assert not missing, missing[:10]
+    c.set_debug_dump(None)
+
+
+@pytest.mark.parametrize("cfg,n_sample", [("c2m", None), ("c3m", 3000), ("c4m", 2500), ("c5m", 2500)])
+def test_minis_fp64_recheck(cfg, n_sample):
+    from paper_2605_10457_gb300.grca import CAST_FP64_RECHECK
+    sc = make_config(cfg)
+    c, ids, tris = _setup(sc, frame=7)
+    d, t = _cast(c, ids, CAST_FP64_RECHECK)
+    assert c.stats()["device_error"] == 0
+    rays = None
+    if n_sample:
+        rays = stratified_rays(sc.sensors, n_sample // len(sc.sensors), seed=3)
+        if sc.stress_rays is not None:
+            rays = np.unique(np.concatenate([rays, sc.stress_rays]))
+    g = _check(sc, tris, d, t, rays)
+    assert g["errors"] == 0, g
+
+
+@pytest.mark.parametrize("d_max", [10.0, 50.0])
+def test_range_cull_c4m(d_max):
+    from paper_2605_10457_gb300.grca import CAST_FP64_RECHECK
+    sc = make_config("c4m")
+    for s in sc.sensors:
+        s.d_min, s.d_max = 0.05, d_max
+    c, ids, tris = _setup(sc, frame=2)
+    d, t = _cast(c, ids, CAST_FP64_RECHECK)
+    assert np.all(d[np.isfinite(d)] <= d_max * (1 + 1e-6))
+    rays = stratified_rays(sc.sensors, 300, seed=5)
+    g = _check(sc, tris, d, t, rays)
+    assert g["errors"] == 0, g
+
+
+def test_backface_cull_c1():
+    from paper_2605_10457_gb300.grca import CAST_CULL_BACKFACE, CAST_FP64_RECHECK
+    sc = scene_c1()
+    c, ids, tris = _setup(sc)
+    d, t = _cast(c, ids, CAST_FP64_RECHECK | CAST_CULL_BACKFACE)
+    g = _check(sc, tris, d, t, cull=True)
+    assert g["errors"] == 0, g
+    d2, t2 = _cast(c, ids, CAST_FP64_RECHECK)
+    assert np.array_equal(t, t2)   # closed outward meshes seen from outside
+
+
+def test_graph_replay_and_vertex_update():
+    from paper_2605_10457_gb300.grca import CAST_FP64_RECHECK, CAST_GRAPH
+    import torch
+    sc = make_config("c2m")
+    c, ids, tris = _setup(sc)
+    out = c.outputs(ids)
+    fl = CAST_FP64_RECHECK
+    c.cast(ids, fl | CAST_GRAPH, out)
+    c.cast(ids, fl | CAST_GRAPH, out)
+    torch.cuda.synchronize()
+    a = out[1].cpu().numpy().view(np.uint32).copy()
+    d_ng, t_ng = _cast(c, ids, fl)
+    assert np.array_equal(a, t_ng)
+    # animate: frame 5 through update_vertices, then replay the same graph
+    tr5 = sc.tris(5)
+    c.update(tr5[sc.n_static:], sc.n_static)
+    c.cast(ids, fl | CAST_GRAPH, out)
+    torch.cuda.synchronize()
+    d5 = out[0].cpu().numpy()
+    t5 = out[1].cpu().numpy().view(np.uint32)
+    d5n, t5n = _cast(c, ids, fl)
+    assert np.array_equal(t5, t5n)
+    rays = stratified_rays(sc.sensors, 2000, seed=9)
+    g = _check(sc, tr5, d5, t5, rays)
+    assert g["errors"] == 0, g
+
+
+def test_pose_change_and_partial_fov():
+    from paper_2605_10457_gb300.grca import CAST_FP64_RECHECK
+    sc = scene_c1()
+    c, ids, tris = _setup(sc)
+    s90 = make_sensor((1.0, 2.0, 1.2), yaw=0.9, channels="c32", n_rays=300, fov_deg=90.0)
+    s270 = make_sensor((-3.0, 1.0, 2.5), yaw=2.0, channels="c64", n_rays=900, fov_deg=270.0, pitch=0.15, roll=0.1)
+    i90, i270 = c.add_sensor(s90), c.add_sensor(s270)
+    # move the first sensor
+    s0 = sc.sensors[0]
+    new = make_sensor((2.5, -1.0, 1.5), yaw=-0.7, channels="uniform16", n_rays=512, pitch=-0.05)
+    c.set_pose(ids[0], new.origin, new.f, new.r, new.u)
+    allids = [ids[0], i90, i270]
+    d, t = _cast(c, allids, CAST_FP64_RECHECK)
+    S = type("S", (), {"sensors": [c.sensors[i] for i in allids]})
+    g = _check(S, tris, d, t)
+    assert g["errors"] == 0, g
+
+
+def test_edge_cases():
+    from paper_2605_10457_gb300.grca import CAST_FP64_RECHECK
+    import torch
+    sens = make_sensor((0.0, 0.0, 1.0), channels="uniform16", n_rays=64)
+    c = _caster()
+    sid = c.add_sensor(sens)
+    # no triangles: all misses
+    c.upload(np.zeros((0, 3, 3), np.float32))
+    d, t = _cast(c, [sid], CAST_FP64_RECHECK)
+    assert np.all(np.isinf(d)) and np.all(t == 0xFFFFFFFF)
+    # zero-area triangles never hit; one valid triangle in front
+    tris = np.array([[[3, 0, 1], [3, 0, 1], [3, 1, 1]],          # repeated vertex
+                     [[3, -1, 0], [3, 0, 1], [3, 1, 2]],         # collinear
+                     [[3, -1, -1], [3, 1, -1], [3, 0, 3]]], np.float32)
+    c.upload(tris)
+    d, t = _cast(c, [sid], CAST_FP64_RECHECK)
+    assert set(np.unique(t).tolist()) <= {2, 0xFFFFFFFF} and np.any(t == 2)
+    # extreme grids: 1024 channels x 64 rays, 4 channels x 32768 rays
+    s1 = make_sensor((0.0, 0.0, 0.0), elev=np.linspace(-1.5, 1.5, 1024), n_rays=64)
+    s2 = make_sensor((0.0, 0.0, 0.0), elev=np.deg2rad([-3.0, -1.0, 1.0, 3.0]), n_rays=32768)
+    tris = tiny_scene(11, n_tris=500, extent=5.0)
+    c2 = _caster()
+    ids = [c2.add_sensor(s1), c2.add_sensor(s2)]
+    c2.upload(tris)
+    d, t = _cast(c2, ids, CAST_FP64_RECHECK)
+    S = type("S", (), {"sensors": [s1, s2]})
+    rays = stratified_rays([s1, s2], 3000, seed=1)
+    g = _check(S, tris, d, t, rays)
+    assert g["errors"] == 0, g
+
+
+def test_capacity_overflow_is_reported():
+    from paper_2605_10457_gb300.grca import CAST_FP64_RECHECK
+    sc = scene_c1()
+    c, ids, tris = _setup(sc, big_pair_capacity=4, chunk_capacity=8, inline_max=4)
+    _cast(c, ids, CAST_FP64_RECHECK)
+    st = c.stats(check=False)
+    assert st["status"] == -4 and st["device_error"] != 0
+    # the next cast with room reports no error
+    c2, ids2, _ = _setup(sc)
+    _cast(c2, ids2, CAST_FP64_RECHECK)
+    assert c2.stats(check=False)["status"] == 0
+
+
+def test_bad_arguments_rejected():
+    from paper_2605_10457_gb300 import grca
+    c = _caster()
+    bad = make_sensor((0, 0, 0), channels="c32", n_rays=64)
+    bad.elev = bad.elev[::-1].copy()   # not ascending
+    with pytest.raises(grca.GrcaError):
+        c.add_sensor(bad)
+    ok = c.add_sensor(make_sensor((0, 0, 0), channels="c32", n_rays=64))
+    with pytest.raises(grca.GrcaError):
+        c.cast([ok + 5], 0)
+    with pytest.raises(grca.GrcaError):
+        c.set_pose(ok, (0, 0, 0), (1, 0, 0), (1, 0, 0), (0, 0, 1))   # not orthonormal
