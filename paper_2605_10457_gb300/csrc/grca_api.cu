@@ -504,6 +504,9 @@ static void fill_sensor(const grca_ctx* ctx, int id, uint32_t ray_off, SensorDev
     s.ray_off = ray_off;
     s.full = h.full ? 1u : 0u;
     s.has_range = (d.d_min > 0.0 || std::isfinite(d.d_max)) ? 1u : 0u;
+    double det = d.f[0] * (d.r[1] * d.u[2] - d.r[2] * d.u[1]) - d.f[1] * (d.r[0] * d.u[2] - d.r[2] * d.u[0]) +
+                 d.f[2] * (d.r[0] * d.u[1] - d.r[1] * d.u[0]);
+    s.hand = det < 0.0 ? -1.f : 1.f;
 }
 
 static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, float* out_dist, uint32_t* out_tri,

@@ -44,6 +44,7 @@ struct SensorDev {
     uint32_t full;        // 1: the azimuth grid closes the circle (period == n_rays)
     uint32_t has_range;   // 1: d_min > 0 or d_max finite
     uint32_t ch_loc;      // offset of this sensor's channels in the cast-local (shared-memory) table
+    float hand;           // det([f; r; u]) = +-1: emitter-frame triple products carry this sign
 };
 
 // Per (triangle, sensor) test setup: everything the per-candidate

@@ -118,7 +118,9 @@ __device__ __forceinline__ V3 rel_origin(const SensorDev& S, V3 v) {
 __device__ __forceinline__ void make_setup(const SensorDev& S, const TriW& T, const V3 w[3], const V3 p[3],
                                            float det, float err_det_abs, PairSetup& st) {
     bool unc = fabsf(det) <= err_det_abs;
-    float fold = det < 0.f ? -1.f : 1.f;
+    // forward hit <=> every emitter-frame edge function has the sign of the
+    // emitter-frame triple product p0.(p1 x p2) = det(B) * det
+    float fold = (det < 0.f ? -1.f : 1.f) * S.hand;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         V3 e = rotB(S.B, T.E[k]);
@@ -841,7 +843,7 @@ __global__ void __launch_bounds__(256) k_test(CastArgs a) {
     warp_add(&a.counters[C_UNCERTAIN], c_unc);
     warp_add(&a.counters[C_TIES], c_ties);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.counters[C_CHUNKS] = n_chunks;
+        a.counters[C_CHUNKS] = *(volatile uint32_t*)&a.qcount[Q_CHUNK];
     }
 }
 
@@ -919,7 +921,7 @@ __global__ void k_recheck_rays(CastArgs a) {
         uint32_t id = (uint32_t)k;
         a.keys64[g] = id == NO_HIT ? KEY_MISS : test_fp64(a, g, id);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_FLAGGED] = nf;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_FLAGGED] = *(volatile uint32_t*)&a.qcount[Q_FLAG];
 }
 
 // R2: FP64 re-test of every queued (ray, triangle) pair
@@ -930,7 +932,7 @@ __global__ void k_recheck_pairs(CastArgs a) {
         unsigned long long k = test_fp64(a, pr.x, pr.y);
         if (k != KEY_MISS) atomicMin(&a.keys64[pr.x], k);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_RECHECK] = np;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_RECHECK] = *(volatile uint32_t*)&a.qcount[Q_RECHECK];
 }
 
 // R3 fused into decode: flagged rays take the FP64 key

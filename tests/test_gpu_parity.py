@@ -262,7 +262,8 @@ def test_bad_arguments_rejected():
     with pytest.raises(grca.GrcaError):
         c.add_sensor(bad)
     ok = c.add_sensor(make_sensor((0, 0, 0), channels="c32", n_rays=64))
+    out = c.outputs([ok])
     with pytest.raises(grca.GrcaError):
-        c.cast([ok + 5], 0)
+        c.cast([ok + 5], 0, out)
     with pytest.raises(grca.GrcaError):
         c.set_pose(ok, (0, 0, 0), (1, 0, 0), (1, 0, 0), (0, 0, 1))   # not orthonormal
