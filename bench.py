@@ -180,6 +180,9 @@ def main():
     ap.add_argument("--ref-rays", type=int, default=48, help="rays per step of the reference arm")
     ap.add_argument("--e2e-steps", type=int, default=0, help="default: steps")
     ap.add_argument("--stats", action="store_true", help="print cast statistics to stderr")
+    ap.add_argument("--capacity", default="large", choices=["large", "small"],
+                    help="device work-queue capacities (small: ~2 GB, for profiler captures)")
+    ap.add_argument("--lean", action="store_true", help="headline leg only (no plain / profile / e2e legs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -202,7 +205,10 @@ def main():
     full0 = np.ascontiguousarray(np.concatenate([sc.static_tris, frames_host[0]], 0))
     frames_dev = torch.from_numpy(np.stack(frames_host, 0)).to(dev)       # [F, nd, 3, 3]
 
-    c = grca.Caster(local, big_pair_capacity=48 << 20, chunk_capacity=512 << 20, recheck_capacity=64 << 20)
+    caps = dict(big_pair_capacity=48 << 20, chunk_capacity=512 << 20, recheck_capacity=64 << 20)
+    if args.capacity == "small":
+        caps = dict(big_pair_capacity=8 << 20, chunk_capacity=48 << 20, recheck_capacity=16 << 20)
+    c = grca.Caster(local, **caps)
     ids = [c.add_sensor(s) for s in sc.sensors]
     c.upload(full0)
     n_rays = sc.n_rays
@@ -261,6 +267,13 @@ def main():
     clocks = clk.stop()
     launches_per_frame = c.last_launch_count()
     st = c.stats(check=False)
+    if args.lean:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": ws * n_rays * args.steps / (ms_b / 1e3) / 1e6,
+                              "unit": "Mrays/s", "ms_per_step": ms_b / args.steps, "lean": True,
+                              "stats": st, "clocks": clocks}), flush=True)
+        c.close()
+        return 0
 
     # --- plain single-sensor FP32 path -----------------------------------------
     ms_p = timed(step_plain, args.steps, max(3, args.warmup // 2))

@@ -297,14 +297,19 @@ __device__ __forceinline__ void edge_elev_extremum(V3 a, V3 b, float& smin, floa
     float ee = e.x * e.x + e.y * e.y + e.z * e.z;
     float num = a.z * ae - e.z * aa;
     float den = e.z * ae - a.z * ee;
-    if (!(fabsf(den) > 0.f)) return;
-    float lam = num / den;
-    if (!(lam > -1e-3f && lam < 1.001f)) return;
+    if (den < 0.f) {
+        num = -num;
+        den = -den;
+    }
+    // lambda* = num/den must lie in (-1e-3, 1.001) (padded edge interior)
+    if (!(den > 0.f) || !(num > -1e-3f * den) || !(num < 1.001f * den)) return;
     V3 m = {a.y * e.z - a.z * e.y, a.z * e.x - a.x * e.z, a.x * e.y - a.y * e.x};
-    float mm = m.x * m.x + m.y * m.y + m.z * m.z;
+    float mh = m.x * m.x + m.y * m.y;
+    float mm = mh + m.z * m.z;
     if (!(mm > 1e-12f * aa * ee)) return;  // edge collinear with the origin: vertices bound it
-    float v = sqrtf((m.x * m.x + m.y * m.y) / mm);
-    float qz = a.z + fminf(fmaxf(lam, 0.f), 1.f) * e.z;
+    float v = sqrtf(mh * __frcp_rn(mm));
+    float lam = fminf(fmaxf(num / den, 0.f), 1.f);
+    float qz = a.z + lam * e.z;
     float tol = 1e-4f * sqrtf(aa + ee);
     if (qz >= -tol) smax = fmaxf(smax, v);
     if (qz <= tol) smin = fminf(smin, -v);
@@ -381,10 +386,46 @@ __device__ __forceinline__ bool ray_interval(const SensorDev& S, float A, float 
     return true;
 }
 
+// azimuth padding of a direction: FP32 errors of p scale with |p|, so the
+// azimuth error scales with |p| / |p_h| = 1 / sqrt(1 - sin^2(elevation))
+__device__ __forceinline__ float az_pad_s(float s) {
+    float c2 = 1.f - s * s;
+    return c2 > 1e-12f ? 16.f * U32 * rsqrtf(c2) : 10.f;
+}
 __device__ __forceinline__ float az_pad(V3 p) {
-    float h = sqrtf(p.x * p.x + p.y * p.y);
-    float r = sqrtf(p.x * p.x + p.y * p.y + p.z * p.z);
-    return h > 0.f ? 16.f * U32 * r / h : 10.f;
+    float h2 = p.x * p.x + p.y * p.y;
+    float r2 = h2 + p.z * p.z;
+    return h2 > 1e-12f * r2 ? 16.f * U32 * sqrtf(r2 / h2) : 10.f;
+}
+
+// angle from a to b in the xy plane, in (-pi, pi]; small angles by the
+// series atan(x) = x - x^3/3 + x^5/5 (error < x^7/7 < 2e-12 for |x| < 0.02)
+__device__ __forceinline__ float rel_angle(V3 a, V3 b) {
+    float cr = cross2(a, b), dt = dot2(a, b);
+    if (dt > 0.f && fabsf(cr) < 0.02f * dt) {
+        float x = cr / dt, x2 = x * x;
+        return x * (1.f - x2 * (0.33333334f - 0.2f * x2));
+    }
+    return atan2f(cr, dt);
+}
+
+// Does the vertical axis through the origin meet the triangle?  Point in the
+// xy-projection, closed, with a margin of 1e-5 |p| plus the FP32 error of the
+// 2-D edge functions.  The bounding-box test keeps triangles whose projection
+// degenerates to a segment (vertical faces seen edge-on) from passing on the
+// edge functions alone.
+__device__ __forceinline__ bool axis_pierces(const V3 p[3]) {
+    float q0 = p[0].x * p[0].x + p[0].y * p[0].y, q1 = p[1].x * p[1].x + p[1].y * p[1].y,
+          q2 = p[2].x * p[2].x + p[2].y * p[2].y;
+    float dm = 1e-5f * sqrtf(fmaxf(q0, fmaxf(q1, q2)));
+    float mnx = fminf(p[0].x, fminf(p[1].x, p[2].x)), mxx = fmaxf(p[0].x, fmaxf(p[1].x, p[2].x));
+    float mny = fminf(p[0].y, fminf(p[1].y, p[2].y)), mxy = fmaxf(p[0].y, fmaxf(p[1].y, p[2].y));
+    if (mnx > dm || mxx < -dm || mny > dm || mxy < -dm) return false;
+    float c0 = cross2(p[0], p[1]), c1 = cross2(p[1], p[2]), c2 = cross2(p[2], p[0]);
+    float t0 = dm * (fabsf(p[1].x - p[0].x) + fabsf(p[1].y - p[0].y)) + 16.f * U32 * (q0 + q1);
+    float t1 = dm * (fabsf(p[2].x - p[1].x) + fabsf(p[2].y - p[1].y)) + 16.f * U32 * (q1 + q2);
+    float t2 = dm * (fabsf(p[0].x - p[2].x) + fabsf(p[0].y - p[2].y)) + 16.f * U32 * (q2 + q0);
+    return (c0 >= -t0 && c1 >= -t1 && c2 >= -t2) || (c0 <= t0 && c1 <= t1 && c2 <= t2);
 }
 
 // Channel span (exact elevation extent, padded) and azimuth span (vertex
@@ -394,20 +435,15 @@ __device__ __forceinline__ bool pair_span(const SensorDev& S, const float2* ch, 
     float smin = 2.f, smax = -2.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        float r = sqrtf(p[k].x * p[k].x + p[k].y * p[k].y + p[k].z * p[k].z);
-        s_v[k] = r > 0.f ? p[k].z / r : 0.f;
+        float r2 = p[k].x * p[k].x + p[k].y * p[k].y + p[k].z * p[k].z;
+        s_v[k] = r2 > 0.f ? p[k].z * rsqrtf(r2) : 0.f;
         smin = fminf(smin, s_v[k]);
         smax = fmaxf(smax, s_v[k]);
     }
     edge_elev_extremum(p[0], p[1], smin, smax);
     edge_elev_extremum(p[1], p[2], smin, smax);
     edge_elev_extremum(p[2], p[0], smin, smax);
-    // does the vertical axis through the origin meet the triangle?
-    float c0 = cross2(p[0], p[1]), c1 = cross2(p[1], p[2]), c2 = cross2(p[2], p[0]);
-    float h0 = sqrtf(p[0].x * p[0].x + p[0].y * p[0].y), h1 = sqrtf(p[1].x * p[1].x + p[1].y * p[1].y),
-          h2 = sqrtf(p[2].x * p[2].x + p[2].y * p[2].y);
-    float t0 = 1e-5f * h0 * h1, t1 = 1e-5f * h1 * h2, t2 = 1e-5f * h2 * h0;
-    bool pierced = (c0 >= -t0 && c1 >= -t1 && c2 >= -t2) || (c0 <= t0 && c1 <= t1 && c2 <= t2);
+    bool pierced = axis_pierces(p);
     if (pierced) {
         if (fmaxf(p[0].z, fmaxf(p[1].z, p[2].z)) > 0.f) smax = 1.f;
         if (fminf(p[0].z, fminf(p[1].z, p[2].z)) < 0.f) smin = -1.f;
@@ -431,9 +467,9 @@ __device__ __forceinline__ bool pair_span(const SensorDev& S, const float2* ch, 
             return true;
         }
     } else {
-        float d1 = atan2f(cross2(p[0], p[1]), dot2(p[0], p[1]));
-        float d2 = atan2f(cross2(p[0], p[2]), dot2(p[0], p[2]));
-        float pad = EPS_T + az_pad(p[0]) + az_pad(p[1]) + az_pad(p[2]);
+        float d1 = rel_angle(p[0], p[1]);
+        float d2 = rel_angle(p[0], p[2]);
+        float pad = EPS_T + az_pad_s(s_v[0]) + az_pad_s(s_v[1]) + az_pad_s(s_v[2]);
         float lo = fminf(0.f, fminf(d1, d2)) - pad, hi = fmaxf(0.f, fmaxf(d1, d2)) + pad;
         if (hi - lo >= 6.2831f) {
             A = sp.a0 - 0.5f * S.period;
@@ -505,13 +541,15 @@ __device__ __forceinline__ void warp_add(unsigned long long* ctr, uint32_t v) {
 }
 
 template <bool RECHECK, bool BRUTE>
-__global__ void __launch_bounds__(256) k_cull(CastArgs a) {
+__global__ void __launch_bounds__(256, 3) k_cull(CastArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     SensorDev* s_sens = reinterpret_cast<SensorDev*>(smem);
     float2* s_ch = reinterpret_cast<float2*>(smem + sizeof(SensorDev) * a.n_sensors);
     size_t off = sizeof(SensorDev) * a.n_sensors + sizeof(float2) * a.total_ch;
     off = (off + 15) & ~size_t(15);
-    float* s_tri = reinterpret_cast<float*>(smem + off);
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    // warp-private staging slice: 32 triangles x 9 floats (+1 float4 of slack)
+    float* s_tri = reinterpret_cast<float*>(smem + off) + wib * (32 * 9 + 4);
 
     for (uint32_t q = threadIdx.x; q < a.n_sensors * (uint32_t)(sizeof(SensorDev) / 4); q += blockDim.x)
         reinterpret_cast<uint32_t*>(s_sens)[q] = reinterpret_cast<const uint32_t*>(a.sensors)[q];
@@ -520,24 +558,26 @@ __global__ void __launch_bounds__(256) k_cull(CastArgs a) {
         const SensorDev& S = s_sens[sn];
         for (uint32_t j = threadIdx.x; j < S.n_ch; j += blockDim.x) s_ch[S.ch_loc + j] = a.ch_sc[S.ch_off + j];
     }
+    __syncthreads();
 
     const bool cull_back = a.flags & 2u;
     const bool dump = a.flags & 16u;
     uint32_t c_live = 0, c_cand = 0, c_inl = 0, c_big = 0, c_tests = 0, c_hits = 0, c_unc = 0, c_ties = 0;
 
-    const uint32_t bsz = blockDim.x;
-    for (uint32_t base = blockIdx.x * bsz; base < a.n_tris; base += gridDim.x * bsz) {
-        __syncthreads();
-        uint32_t cnt = min(bsz, a.n_tris - base);
-        // triangles are 36 B; a block's slice starts 16-B aligned (bsz % 4 == 0)
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t gwarp = ((blockIdx.x * blockDim.x) >> 5) + wib;
+    for (uint32_t base = gwarp * 32; base < a.n_tris; base += n_warps * 32) {
+        uint32_t cnt = min(32u, a.n_tris - base);
+        // a warp's 32 triangles are 1152 B, 16-B aligned (base % 4 == 0)
         const float4* src = reinterpret_cast<const float4*>(a.tris + 9ull * base);
         uint32_t n4 = (cnt * 9u + 3u) >> 2;
-        for (uint32_t q = threadIdx.x; q < n4; q += bsz) reinterpret_cast<float4*>(s_tri)[q] = src[q];
-        __syncthreads();
-        if (threadIdx.x >= cnt) continue;
-        const uint32_t tri = base + threadIdx.x;
+        __syncwarp();
+        for (uint32_t q = lane; q < n4; q += 32) reinterpret_cast<float4*>(s_tri)[q] = __ldcs(src + q);
+        __syncwarp();
+        if (lane >= cnt) continue;
+        const uint32_t tri = base + lane;
         TriW T;
-        tri_world(s_tri + 9 * threadIdx.x, T);
+        tri_world(s_tri + 9 * lane, T);
         if (T.n.x == 0.f && T.n.y == 0.f && T.n.z == 0.f) continue;  // zero area: never hit
 
         for (uint32_t sn = 0; sn < a.n_sensors; ++sn) {
@@ -645,7 +685,7 @@ __device__ __forceinline__ bool channel_span_rel(const V3 p[3], const float s_v[
     hi = -1e30f;
     V3 p0 = p[0];
     auto include = [&](V3 q, float extra) {
-        float ang = atan2f(cross2(p0, q), dot2(p0, q));
+        float ang = rel_angle(p0, q);
         float pad = EPS_ROW + az_pad(q) + extra;
         lo = fminf(lo, ang - pad);
         hi = fmaxf(hi, ang + pad);
@@ -740,8 +780,8 @@ __global__ void __launch_bounds__(256) k_expand(CastArgs a) {
         float s_v[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            float r = sqrtf(p[k].x * p[k].x + p[k].y * p[k].y + p[k].z * p[k].z);
-            s_v[k] = r > 0.f ? p[k].z / r : 0.f;
+            float r2 = p[k].x * p[k].x + p[k].y * p[k].y + p[k].z * p[k].z;
+            s_v[k] = r2 > 0.f ? p[k].z * rsqrtf(r2) : 0.f;
         }
         const int n = (int)S.n_rays;
         const bool full_pair = P.n_r >= (uint32_t)n;
@@ -953,7 +993,7 @@ __global__ void k_decode(CastArgs a, int recheck) {
 size_t cull_smem_bytes(const CastArgs& a, const LaunchCfg& cfg) {
     size_t off = sizeof(SensorDev) * a.n_sensors + sizeof(float2) * a.total_ch;
     off = (off + 15) & ~size_t(15);
-    return off + sizeof(float) * 9 * (size_t)cfg.cull_block + 16;
+    return off + sizeof(float) * (32 * 9 + 4) * (size_t)(cfg.cull_block / 32);
 }
 
 template <bool R, bool B>

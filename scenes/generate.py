@@ -355,31 +355,31 @@ def scene_c1(seed: int = 1) -> Scene:
     return Scene("c1", [sensor], np.ascontiguousarray(np.concatenate(parts, 0)))
 
 
-def _object_field(rng, n_objects, tris_per_obj, area_lo, area_hi, r_min, r_max, keepout, max_surface=6000.0):
-    """Closed static objects (boxes and ellipsoids) whose triangle area is
-    log-uniform in [area_lo, area_hi] m^2 per object, each with about
-    `tris_per_obj` triangles (fewer when the surface would exceed max_surface)."""
+def _object_field(rng, tri_budget, surf_lo, surf_hi, area_lo, area_hi, r_min, r_max, keepout, max_tris=20000):
+    """Closed static objects (boxes and ellipsoids) until `tri_budget`
+    triangles: surface log-uniform in [surf_lo, surf_hi] m^2, triangle area
+    log-uniform in [area_lo, area_hi] m^2 per object (clipped so an object has
+    12 .. max_tris triangles), yaw uniform, centres uniform in the annulus."""
     parts = []
-    centres = _place_disk(rng, n_objects, r_min, r_max, keepout, 4.0)
-    for k in range(n_objects):
+    total = 0
+    while total < tri_budget:
+        surf = math.exp(rng.uniform(math.log(surf_lo), math.log(surf_hi)))
         a_t = math.exp(rng.uniform(math.log(area_lo), math.log(area_hi)))
-        surf = min(a_t * tris_per_obj, max_surface)
-        n_t = max(12, int(round(surf / a_t)))
+        a_t = min(max(a_t, surf / max_tris), surf / 12.0)
+        n_t = max(12, min(max_tris, tri_budget - total, int(round(surf / a_t))))
         aspect = rng.uniform(0.4, 1.0, 3)
+        cx, cy = _place_disk(rng, 1, r_min, r_max, keepout, 4.0)[0]
         if rng.uniform() < 0.5:
-            # box: surface 2(ab+bc+ca) with sides s*aspect
             q = 2.0 * (aspect[0] * aspect[1] + aspect[1] * aspect[2] + aspect[2] * aspect[0])
-            s = math.sqrt(surf / q)
-            size = s * aspect
+            size = math.sqrt(surf / q) * aspect
             m = box_for_count(size, n_t)
             zc = size[2] / 2
         else:
-            # ellipsoid: surface ~ 4 pi (mean radius)^2
-            s = math.sqrt(surf / (4.0 * math.pi * float(np.mean(aspect * aspect))))
-            radii = s * aspect
+            radii = math.sqrt(surf / (4.0 * math.pi * float(np.mean(aspect * aspect)))) * aspect
             m = ellipsoid_for_count(radii, n_t)
             zc = radii[2] * rng.uniform(0.3, 1.2)
-        parts.append(gather(m, (centres[k][0], centres[k][1], zc), yaw_matrix(rng.uniform(-math.pi, math.pi))))
+        parts.append(gather(m, (cx, cy, zc), yaw_matrix(rng.uniform(-math.pi, math.pi))))
+        total += m.faces.shape[0]
     return parts
 
 
@@ -405,17 +405,24 @@ def _rigid_movers(rng, n_inst, tris_per_obj, kind, r_min, r_max, keepout, scale_
     return groups
 
 
-def _deformers(rng, n_obj, tris_per_obj, r_min, r_max, keepout):
+def _deformers(rng, n_obj, tris_per_obj, r_min, r_max, keepout, radii_range=(0.5, 3.0)):
     out = []
     centres = _place_disk(rng, n_obj, r_min, r_max, keepout, 5.0)
     for k in range(n_obj):
-        radii = rng.uniform(0.5, 3.0, 3)
+        radii = rng.uniform(radii_range[0], radii_range[1], 3)
         m = ellipsoid_for_count(radii, tris_per_obj)
         nrm = vertex_normals_ellipsoid(m.verts, radii)
         amp = rng.uniform(0.05, 0.5)
         c0 = np.array([centres[k][0], centres[k][1], radii[2] + amp + rng.uniform(0.0, 2.0)])
         out.append(DeformObject(m, nrm, c0, amp, rng.uniform(0.5, 2.0), rng.normal(0.0, 1.0, 3)))
     return out
+
+
+# C4/C5 static objects: ~10.8 M triangles of closed objects, surface 0.5-100 m^2,
+# triangle area log-uniform 1e-4..1 m^2 (mean ~ the paper's Power Plant, 384 cm^2)
+C45_STATIC = 10_800_000
+C45_SURF = (0.5, 100.0)
+C45_AREA = (1e-4, 1.0)
 
 
 def rig_c4(d_max=math.inf, d_min=0.05):
@@ -436,17 +443,18 @@ def rig_c5(d_min=0.05):
     return [make_sensor(p, elev=t, n_rays=4096, d_min=d_min) for p in slots]
 
 
-def _big_scene(name, sensors, seed, scale, ground_n, n_static_obj, static_tpo, n_rigid, rigid_tpo,
-               n_deform, deform_tpo, area=(1e-4, 10.0), extent=100.0, n_frames=50):
+def _big_scene(name, sensors, seed, ground_n, static_budget, surf, area, n_rigid, rigid_tpo, n_deform,
+               deform_tpo, extent=100.0, n_frames=50, mover_scale=(0.3, 1.2), deform_radii=(0.3, 1.5)):
     rng = np.random.default_rng(seed)
     keep = [(float(s.origin[0]), float(s.origin[1])) for s in sensors]
     parts = []
     if ground_n > 0:
         parts.append(gather(grid_mesh(-extent, extent, -extent, extent, ground_n, ground_n)))
-    parts += _object_field(rng, n_static_obj, static_tpo, area[0], area[1], 8.0, extent * 0.95, keep)
+    if static_budget > 0:
+        parts += _object_field(rng, static_budget, surf[0], surf[1], area[0], area[1], 8.0, extent * 0.95, keep)
     static = np.ascontiguousarray(np.concatenate(parts, 0)) if parts else np.zeros((0, 3, 3), np.float32)
-    rigid = _rigid_movers(rng, n_rigid, rigid_tpo, "mixed", 10.0, extent * 0.8, keep, 0.5, 2.0) if n_rigid else []
-    deform = _deformers(rng, n_deform, deform_tpo, 8.0, extent * 0.8, keep) if n_deform else []
+    rigid = _rigid_movers(rng, n_rigid, rigid_tpo, "mixed", 10.0, extent * 0.8, keep, *mover_scale) if n_rigid else []
+    deform = _deformers(rng, n_deform, deform_tpo, 8.0, extent * 0.8, keep, deform_radii) if n_deform else []
     return Scene(name, sensors, static, rigid, deform, n_frames=n_frames)
 
 
@@ -510,8 +518,10 @@ def scene_c3(seed: int = 3, mini: bool = False) -> Scene:
     s = [make_sensor((0.0, 0.0, 1.8), elev=t, n_rays=nr),
          make_sensor((2.0, 0.0, 1.8), elev=t, n_rays=nr, fov_deg=180.0)]
     if mini:
-        return _big_scene("c3m", s, seed, 1, 30, 8, 3500, 0, 0, 4, 5000)
-    return _big_scene("c3", s, seed, 1, 300, 806, 3500, 0, 0, 400, 5000)
+        return _big_scene("c3m", s, seed, 30, 28_000, (1.0, 300.0), (1e-4, 10.0), 0, 0, 4, 5000,
+                          deform_radii=(0.5, 3.0))
+    return _big_scene("c3", s, seed, 300, 2_820_000, (1.0, 300.0), (1e-4, 10.0), 0, 0, 400, 5000,
+                      deform_radii=(0.5, 3.0))
 
 
 def scene_c4(seed: int = 4, d_max=math.inf, mini: bool = False) -> Scene:
@@ -525,8 +535,8 @@ def scene_c4(seed: int = 4, d_max=math.inf, mini: bool = False) -> Scene:
             s.n_rays //= 4
             s.dtheta *= 4
             s.theta0 = -math.pi if abs(s.n_rays * s.dtheta - 2 * math.pi) < 1e-9 else -(s.n_rays // 2) * s.dtheta
-        return _big_scene("c4m", sens, seed, 1, 140, 30, 3500, 12, 5000, 6, 5000)
-    return _big_scene("c4", sens, seed, 1, 1000, 3400, 3500, 1200, 5000, 600, 5000)
+        return _big_scene("c4m", sens, seed, 140, 108_000, C45_SURF, C45_AREA, 12, 5000, 6, 5000)
+    return _big_scene("c4", sens, seed, 1000, C45_STATIC, C45_SURF, C45_AREA, 1200, 5000, 600, 5000)
 
 
 def stress_set(sensors: List[Sensor], rng, n_items: int):
@@ -618,9 +628,9 @@ def scene_c5(seed: int = 5, mini: bool = False, n_stress: int = 1500) -> Scene:
             s.elev = subsample_channels(s.elev, 4)
             s.n_rays //= 4
             s.dtheta *= 4
-        sc = _big_scene("c5m", sens, seed, 1, 140, 30, 3500, 12, 5000, 6, 5000, n_frames=60)
+        sc = _big_scene("c5m", sens, seed, 140, 108_000, C45_SURF, C45_AREA, 12, 5000, 6, 5000, n_frames=60)
     else:
-        sc = _big_scene("c5", sens, seed, 1, 1000, 3400, 3500, 1200, 5000, 600, 5000, n_frames=60)
+        sc = _big_scene("c5", sens, seed, 1000, C45_STATIC, C45_SURF, C45_AREA, 1200, 5000, 600, 5000, n_frames=60)
     rng = np.random.default_rng(seed + 1000)
     st, rays = stress_set(sens, rng, n_stress if not mini else max(30, n_stress // 50))
     sc.static_tris = np.ascontiguousarray(np.concatenate([sc.static_tris, st], 0))
