@@ -182,6 +182,32 @@ grca_status grca_cast_host(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_
 grca_status grca_autotune(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_sensors, float* out_dist,
                           uint32_t* out_tri, uint32_t flags, void* stream, float* out_ms);
 
+/* Allocation-free cast of one sensor.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc (for example
+ * code running inside an allocator or memory-pool callback, a plugin whose
+ * host forbids device allocations after start-up, or a real-time loop that
+ * must not wait on the driver's allocator).  It needs no context and
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * Its scratch memory (per-ray closest-hit keys, ray tables, counters) is one
+ * fixed device array of about 2.4 MB inside the library, present on every
+ * GPU that loads the library until the process exits.
+ *   sensor   : as for grca_create_sensor (read during the call only).
+ *   tris     : DEVICE pointer, n_tris FP32 triangles [n][3][3], 16-byte aligned.
+ *   out_dist, out_tri : DEVICE arrays of n_channels*n_rays entries, same
+ *              layout and miss convention as grca_cast.
+ *   flags    : 0 or GRCA_CAST_CULL_BACKFACE; the plain FP32 test is used.
+ * Limits: n_channels <= 256, n_rays <= 32768, n_channels*n_rays <= 262144;
+ * larger sizes return GRCA_ERR_CAPACITY, other bad arguments
+ * GRCA_ERR_INVALID_ARG.
+ * The first call on a device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call on a device shares the one
+ * array (each call resets what must start empty): calls that overlap on the
+ * GPU (different streams, or different host threads) race and corrupt each
+ * other's results. */
+grca_status grca_cast_noalloc(const grca_sensor_desc* sensor, const float* tris, uint32_t n_tris, float* out_dist,
+                              uint32_t* out_tri, uint32_t flags, void* stream);
+
 /* Debug dump for GRCA_CAST_DUMP_CANDIDATES: a DEVICE buffer of `capacity`
  * (global ray id, triangle id) uint32 pairs and a DEVICE uint32 counter
  * (caller zeroes it).  Pass NULLs to detach. */

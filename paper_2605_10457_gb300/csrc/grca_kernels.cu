@@ -27,6 +27,8 @@
 // ray passes between them.  t = ((v0-o).n) / (d.n).
 #include <cooperative_groups.h>
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -1070,3 +1072,177 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
 }
 
 }  // namespace grca
+
+// ===========================================================================
+// Allocation-free cast (grca_cast_noalloc)
+//
+// Some callers cannot call cudaMalloc: code running inside a host-side
+// allocator or memory-pool callback, a plugin whose host framework forbids
+// device allocations after start-up, or a real-time loop that must not block
+// on the driver's allocator.  For them this entry point keeps its scratch
+// memory (per-ray closest-hit keys, the ray direction tables, the sensor
+// descriptor and the counters) in one fixed, file-scope device array that
+// exists from module load until process exit on every GPU that loads the
+// library.  It runs the same culling and decode kernels as grca_cast, with
+// all candidate spans tested inline and the plain FP32 test.
+// ===========================================================================
+namespace grca {
+
+constexpr uint32_t NOALLOC_MAX_RAYS = 262144;      // channels x rays per call
+constexpr uint32_t NOALLOC_MAX_CHANNELS = 256;
+constexpr uint32_t NOALLOC_MAX_AZIMUTH = (uint32_t)MAX_RAYS;
+
+struct NoallocLayout {
+    static constexpr size_t keys = 0;                                              // u64 x max rays
+    static constexpr size_t az = keys + sizeof(unsigned long long) * NOALLOC_MAX_RAYS;  // float2 x max azimuth
+    static constexpr size_t ch = az + sizeof(float2) * NOALLOC_MAX_AZIMUTH;             // float2 x max channels
+    static constexpr size_t sensor = ch + sizeof(float2) * NOALLOC_MAX_CHANNELS;        // one SensorDev
+    static constexpr size_t counters = (sensor + sizeof(SensorDev) + 255) & ~size_t(255);  // u64 x C_NUM
+    static constexpr size_t qcount = counters + sizeof(unsigned long long) * C_NUM;        // u32 x Q_NUM
+    static constexpr size_t error = qcount + sizeof(uint32_t) * Q_NUM;                     // u32
+    static constexpr size_t total = (error + sizeof(uint32_t) + 255) & ~size_t(255);
+};
+
+// The scratch array (about 2.4 MB).  Host code must not use this symbol as a
+// device address; it obtains the address with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NoallocLayout::total];
+
+struct NoallocParams {
+    SensorDev s;
+    float2 ch[NOALLOC_MAX_CHANNELS];
+    double theta0, dtheta;
+};
+
+// fill the sensor descriptor, channel and azimuth tables and reset the keys,
+// counters and error word of the scratch array
+__global__ void k_noalloc_prepare(NoallocParams P, unsigned char* scratch) {
+    uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(scratch + NoallocLayout::keys);
+    float2* az = reinterpret_cast<float2*>(scratch + NoallocLayout::az);
+    float2* ch = reinterpret_cast<float2*>(scratch + NoallocLayout::ch);
+    uint32_t n_total = P.s.n_ch * P.s.n_rays;
+    for (uint32_t g = tid; g < n_total; g += stride) keys[g] = KEY_MISS;
+    for (uint32_t i = tid; i < P.s.n_rays; i += stride) {
+        double sn, cs;
+        sincos(P.theta0 + (double)i * P.dtheta, &sn, &cs);
+        az[i] = make_float2((float)sn, (float)cs);
+    }
+    for (uint32_t j = tid; j < P.s.n_ch; j += stride) ch[j] = P.ch[j];
+    if (tid == 0) *reinterpret_cast<SensorDev*>(scratch + NoallocLayout::sensor) = P.s;
+    if (tid < C_NUM) reinterpret_cast<unsigned long long*>(scratch + NoallocLayout::counters)[tid] = 0ull;
+    if (tid < Q_NUM) reinterpret_cast<uint32_t*>(scratch + NoallocLayout::qcount)[tid] = 0u;
+    if (tid == 0) *reinterpret_cast<uint32_t*>(scratch + NoallocLayout::error) = 0u;
+}
+
+}  // namespace grca
+
+#include <mutex>
+
+#include "grca.h"
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoallocMaxDevices] = {};   // device address of the scratch array, per device index
+int g_noalloc_sm[kNoallocMaxDevices] = {};
+}  // namespace
+
+extern "C" grca_status grca_cast_noalloc(const grca_sensor_desc* d, const float* tris, uint32_t n_tris,
+                                         float* out_dist, uint32_t* out_tri, uint32_t flags, void* stream) {
+    using namespace grca;
+    if (!d || !d->elev_rad || !out_dist || !out_tri || (!tris && n_tris)) return GRCA_ERR_INVALID_ARG;
+    if (flags & ~(uint32_t)GRCA_CAST_CULL_BACKFACE) return GRCA_ERR_INVALID_ARG;
+    if (d->n_channels < 1 || d->n_rays < 1 || !(d->dtheta > 0.0) || !std::isfinite(d->theta0) ||
+        d->n_rays * d->dtheta > 2 * M_PI + 1e-9 || !(d->d_min >= 0.0) || !(d->d_max >= d->d_min))
+        return GRCA_ERR_INVALID_ARG;
+    for (uint32_t j = 0; j < d->n_channels && j < NOALLOC_MAX_CHANNELS; ++j)
+        if (!std::isfinite(d->elev_rad[j]) || std::fabs(d->elev_rad[j]) >= M_PI / 2 ||
+            (j > 0 && !(d->elev_rad[j] > d->elev_rad[j - 1])))
+            return GRCA_ERR_INVALID_ARG;
+    // sizes beyond the fixed scratch array are rejected
+    if (d->n_channels > NOALLOC_MAX_CHANNELS || d->n_rays > NOALLOC_MAX_AZIMUTH ||
+        (uint64_t)d->n_channels * d->n_rays > NOALLOC_MAX_RAYS)
+        return GRCA_ERR_CAPACITY;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return GRCA_ERR_CUDA;
+    unsigned char* scratch = nullptr;
+    int n_sm = 0;
+    {
+        // set-up, once per device, with that device current: the device address
+        // of the scratch array (the host-side symbol is only a stand-in)
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GRCA_ERR_CUDA;
+            int sm = 0;
+            if (cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GRCA_ERR_CUDA;
+            g_noalloc_sm[dev] = sm;
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+        n_sm = g_noalloc_sm[dev];
+    }
+    NoallocParams P;
+    memset(&P, 0, sizeof(P));
+    SensorDev& s = P.s;
+    for (int k = 0; k < 3; ++k) {
+        s.o64[k] = d->origin[k];
+        s.B64[k] = d->f[k];
+        s.B64[3 + k] = d->r[k];
+        s.B64[6 + k] = d->u[k];
+        float hi = (float)d->origin[k];
+        s.o_hi[k] = hi;
+        s.o_lo[k] = (float)(d->origin[k] - (double)hi);
+    }
+    for (int k = 0; k < 9; ++k) s.B[k] = (float)s.B64[k];
+    s.d_min64 = d->d_min;
+    s.d_max64 = d->d_max;
+    s.theta0 = (float)d->theta0;
+    s.dtheta = (float)d->dtheta;
+    s.inv_dtheta = (float)(1.0 / d->dtheta);
+    s.d_min = (float)d->d_min;
+    s.d_max = std::isfinite(d->d_max) ? (float)d->d_max : INFINITY;
+    s.period = (float)(2 * M_PI / d->dtheta);
+    s.n_ch = d->n_channels;
+    s.n_rays = d->n_rays;
+    s.full = std::fabs(d->n_rays * d->dtheta - 2 * M_PI) <= 1e-9 ? 1u : 0u;
+    s.has_range = (d->d_min > 0.0 || std::isfinite(d->d_max)) ? 1u : 0u;
+    double det = d->f[0] * (d->r[1] * d->u[2] - d->r[2] * d->u[1]) - d->f[1] * (d->r[0] * d->u[2] - d->r[2] * d->u[0]) +
+                 d->f[2] * (d->r[0] * d->u[1] - d->r[1] * d->u[0]);
+    s.hand = det < 0.0 ? -1.f : 1.f;
+    for (uint32_t j = 0; j < d->n_channels; ++j) {
+        double e = d->elev_rad[j];
+        P.ch[j] = make_float2((float)std::sin(e), (float)std::cos(e));
+    }
+    P.theta0 = d->theta0;
+    P.dtheta = d->dtheta;
+
+    CastArgs a;
+    memset(&a, 0, sizeof(a));
+    a.tris = tris;
+    a.n_tris = n_tris;
+    a.n_sensors = 1;
+    a.sensors = reinterpret_cast<const SensorDev*>(scratch + NoallocLayout::sensor);
+    a.ch_sc = reinterpret_cast<const float2*>(scratch + NoallocLayout::ch);
+    a.az_sc = reinterpret_cast<const float2*>(scratch + NoallocLayout::az);
+    a.total_ch = d->n_channels;
+    a.n_rays_total = d->n_channels * d->n_rays;
+    a.keys = reinterpret_cast<unsigned long long*>(scratch + NoallocLayout::keys);
+    a.qcount = reinterpret_cast<uint32_t*>(scratch + NoallocLayout::qcount);
+    a.counters = reinterpret_cast<unsigned long long*>(scratch + NoallocLayout::counters);
+    a.error = reinterpret_cast<uint32_t*>(scratch + NoallocLayout::error);
+    a.flags = flags;
+    a.inline_max = 0xFFFFFFFFu;  // every span tested inline: no deferred-pair queue is needed
+    a.out_dist = out_dist;
+    a.out_tri = out_tri;
+    LaunchCfg cfg;
+    cudaStream_t st = (cudaStream_t)stream;
+    int blocks = (int)std::min<uint32_t>((a.n_rays_total + 255) / 256, (uint32_t)n_sm * 8);
+    k_noalloc_prepare<<<std::max(blocks, 1), 256, 0, st>>>(P, scratch);
+    size_t smem = cull_smem_bytes(a, cfg);
+    uint32_t max_blocks = (n_tris + cfg.cull_block - 1) / cfg.cull_block;
+    int cull_grid = (int)std::min<uint32_t>(std::max<uint32_t>(max_blocks, 1u), (uint32_t)(n_sm * cfg.cull_blocks_per_sm));
+    k_cull<false, false><<<cull_grid, cfg.cull_block, smem, st>>>(a);
+    k_decode<<<std::max(blocks, 1), 256, 0, st>>>(a, 0);
+    return cudaGetLastError() == cudaSuccess ? GRCA_OK : GRCA_ERR_CUDA;
+}

@@ -59,7 +59,7 @@ _LIB = None
 EXPORTS = ["grca_create", "grca_destroy", "grca_create_sensor", "grca_set_sensor_pose", "grca_upload_triangles",
            "grca_update_vertices", "grca_cast", "grca_cast_host", "grca_autotune", "grca_set_debug_dump",
            "grca_get_stats", "grca_last_launch_count", "grca_profile_enable", "grca_profile_read",
-           "grca_status_string", "grca_last_cuda_error"]
+           "grca_status_string", "grca_last_cuda_error", "grca_cast_noalloc"]
 
 
 def library_path() -> str:
@@ -106,12 +106,33 @@ def _lib_handle(build_if_missing: bool = True):
     lib.grca_profile_read.argtypes = [P, u32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_uint64),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32)]
     lib.grca_profile_read.restype = i32
+    lib.grca_cast_noalloc.argtypes = [ctypes.POINTER(grca_sensor_desc), P, u32, P, P, u32, P]
+    lib.grca_cast_noalloc.restype = i32
     lib.grca_status_string.argtypes = [i32]
     lib.grca_status_string.restype = ctypes.c_char_p
     lib.grca_last_cuda_error.argtypes = [P]
     lib.grca_last_cuda_error.restype = ctypes.c_char_p
     _LIB = lib
     return lib
+
+
+def sensor_desc(s):
+    """grca_sensor_desc for a scenes.Sensor; returns (desc, elevation array kept alive by the caller)."""
+    elev = np.ascontiguousarray(s.elev, dtype=np.float64)
+    d = grca_sensor_desc()
+    for k in range(3):
+        d.origin[k] = float(s.origin[k])
+        d.f[k] = float(s.f[k])
+        d.r[k] = float(s.r[k])
+        d.u[k] = float(s.u[k])
+    d.elev_rad = elev.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.n_channels = elev.shape[0]
+    d.n_rays = int(s.n_rays)
+    d.theta0 = float(s.theta0)
+    d.dtheta = float(s.dtheta)
+    d.d_min = float(s.d_min)
+    d.d_max = float(s.d_max)
+    return d, elev
 
 
 def _stream_ptr(stream) -> Optional[int]:
