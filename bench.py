@@ -35,8 +35,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Mrays/s and ms/frame (8x128x4096 LiDARs, 22M tris), batched vs plain, oracle-exact"
-F_CULL = 200.0   # FP32 flops per (triangle, sensor) pair in the culling pass
-F_TEST = 30.0    # FP32 flops per candidate ray-triangle test
+F_CULL_A = 100.0  # FP32 flops per (triangle, sensor) pair: transform + elevation range + channel search
+F_CULL_B = 100.0  # FP32 flops per surviving pair: emitter frame + azimuth range + ray interval (+ setup)
+F_TEST = 30.0     # FP32 flops per candidate ray-triangle test
 TRI_BYTES = 36.0
 
 
@@ -207,7 +208,8 @@ def main():
 
     caps = dict(big_pair_capacity=48 << 20, chunk_capacity=512 << 20, recheck_capacity=64 << 20)
     if args.capacity == "small":
-        caps = dict(big_pair_capacity=8 << 20, chunk_capacity=48 << 20, recheck_capacity=16 << 20)
+        caps = dict(big_pair_capacity=8 << 20, chunk_capacity=48 << 20, recheck_capacity=16 << 20,
+                    survivor_capacity=96 << 20)
     c = grca.Caster(local, **caps)
     ids = [c.add_sensor(s) for s in sc.sensors]
     c.upload(full0)
@@ -323,19 +325,23 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = fp32_peak_tflops(sm_max)
     pairs = st_prof["pairs"]
-    if dom_name == "k_cull":
-        flops = pairs * F_CULL + st_prof["candidates_inline"] * F_TEST
+    if dom_name == "k_cull_a":
+        flops = pairs * F_CULL_A
+    elif dom_name == "k_cull_b":
+        flops = st_prof["survivors"] * F_CULL_B + st_prof["candidates_inline"] * F_TEST
     elif dom_name == "k_test":
-        flops = (st_prof["tests"]) * F_TEST
+        flops = (st_prof["tests"] - st_prof["candidates_inline"]) * F_TEST
     else:
         flops = 0.0
     achieved = flops / (avg_ms / 1e3) / 1e12 if flops else 0.0
-    hbm_achieved = (sc.n_tris * TRI_BYTES) / (prof.get("k_cull", {"total_ms": 1})["total_ms"]
-                                               / max(1, prof.get("k_cull", {"launches": 1})["launches"]) / 1e3) / 1e9
+    ka = prof.get("k_cull_a", {"total_ms": 1.0, "launches": 1})
+    hbm_achieved = (sc.n_tris * TRI_BYTES) / (ka["total_ms"] / max(1, ka["launches"]) / 1e3) / 1e9
     roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak if fp32_peak else None, "traffic": None,
                 "peak_source": f"FP32 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (unit counts and max clock)",
-                "algorithmic": f"{F_CULL:.0f} flop/(tri,sensor) pair + {F_TEST:.0f} flop/inline test",
+                "algorithmic": {"k_cull_a": f"{F_CULL_A:.0f} flop per (tri, sensor) pair",
+                                "k_cull_b": f"{F_CULL_B:.0f} flop per surviving pair + {F_TEST:.0f} per inline test",
+                                "k_test": f"{F_TEST:.0f} flop per queued test"},
                 "avg_launch_ms": avg_ms,
                 "hbm_vertex_stream_gbs": hbm_achieved, "hbm_peak_gbs": peaks.get("hbm_gbs"),
                 "hbm_peak_source": src}
@@ -368,7 +374,8 @@ def main():
         "cpu_baseline": cpu,
         "clocks": clocks,
         "kernel_ms": kernel_ms,
-        "stats": {k: st_prof[k] for k in ("pairs", "pairs_live", "candidates", "candidates_inline", "big_pairs",
+        "stats": {k: st_prof[k] for k in ("pairs", "survivors", "pairs_live", "candidates", "candidates_inline",
+                                          "big_pairs",
                                           "chunks", "tests", "hits", "uncertain", "ties", "flagged_rays",
                                           "recheck_pairs")},
         "autotune_ms": tune_ms,

@@ -82,6 +82,8 @@ typedef struct {
     uint32_t chunk_rays;         /* rays per test chunk (default 64) */
     uint32_t cull_block;         /* threads per culling block (default 256) */
     uint32_t cull_blocks_per_sm; /* resident culling blocks per SM (default 4) */
+    uint64_t survivor_capacity;  /* max (triangle, sensor) pairs passing the elevation cull per cast
+                                    (default 256M, 8 B each; the queue grows to n_tris * n_sensors up to it) */
 } grca_options;
 
 /* One spinning LiDAR (Sec. 3.1, Eq. ray_dir and the centred angle grid).
@@ -114,6 +116,7 @@ typedef struct {
 typedef struct {
     uint64_t pairs;           /* (triangle, sensor) pairs visited = n_sensors * n_tris */
     uint64_t pairs_live;      /* pairs whose candidate span is non-empty */
+    uint64_t survivors;       /* pairs that passed the elevation (channel-span) cull */
     uint64_t candidates;      /* (channel, ray) candidates in the pair spans */
     uint64_t candidates_inline; /* of which tested inline by the culling pass */
     uint64_t big_pairs;       /* pairs deferred to the per-channel span pass */
@@ -227,8 +230,8 @@ uint32_t grca_last_launch_count(grca_ctx* ctx);
 grca_status grca_profile_enable(grca_ctx* ctx, int enable);
 
 /* Totals since grca_profile_enable: for kernel k < min(max, *n_out) of the
- * frame sequence (k_init, k_cull, k_expand, k_test, k_recheck_rays,
- * k_recheck_pairs, k_decode), its name (static string), number of launches and
+ * frame sequence (k_init, k_cull_a, k_cull_b, k_expand, k_test,
+ * k_recheck_rays, k_recheck_pairs, k_decode), its name (static string), number of launches and
  * summed device time in ms.  Synchronizes with the recorded events.
  * *n_out receives the number of kernel kinds. */
 grca_status grca_profile_read(grca_ctx* ctx, uint32_t max, const char** names, uint64_t* launches,

@@ -77,9 +77,13 @@ struct grca_ctx {
     double2* d_ch64 = nullptr;
     float2* d_az = nullptr;
     double2* d_az64 = nullptr;
+    uint16_t* d_lut = nullptr;
     std::vector<uint32_t> ch_off, az_off;
+    std::vector<float> lut_lo, lut_inv_w;
     bool tables_dirty = true;
 
+    unsigned long long* d_surv = nullptr;
+    size_t surv_cap = 0;
     unsigned long long* d_keys = nullptr;
     unsigned long long* d_keys64 = nullptr;
     uint32_t* d_flag_bits = nullptr;
@@ -228,7 +232,9 @@ grca_status grca_create(grca_ctx** out, int device, const grca_options* opt) {
     if (!o.chunk_rays) o.chunk_rays = 64;
     if (!o.cull_block) o.cull_block = 256;
     if (!o.cull_blocks_per_sm) o.cull_blocks_per_sm = 4;
+    if (!o.survivor_capacity) o.survivor_capacity = 256u << 20;
     if (o.big_pair_capacity > 0xFFFFFFFFull || o.chunk_capacity > 0xFFFFFFFFull || o.recheck_capacity > 0xFFFFFFFFull ||
+        o.survivor_capacity > 0xFFFFFFFFull ||
         o.cull_block % 32 || o.cull_block > 256 || o.cull_block < 32 || o.chunk_rays > 4096) {
         delete ctx;
         return GRCA_ERR_INVALID_ARG;
@@ -296,10 +302,12 @@ void grca_destroy(grca_ctx* ctx) {
     cudaFree(ctx->d_ch64);
     cudaFree(ctx->d_az);
     cudaFree(ctx->d_az64);
+    cudaFree(ctx->d_lut);
     cudaFree(ctx->d_keys);
     cudaFree(ctx->d_keys64);
     cudaFree(ctx->d_flag_bits);
     cudaFree(ctx->d_flag_list);
+    cudaFree(ctx->d_surv);
     cudaFree(ctx->d_big);
     cudaFree(ctx->d_setups);
     cudaFree(ctx->d_chunks);
@@ -417,15 +425,26 @@ static grca_status ensure_tables(grca_ctx* ctx, cudaStream_t st) {
     std::vector<double2> ch64;
     std::vector<float2> az;
     std::vector<double2> az64;
+    std::vector<uint16_t> lut;
     ctx->ch_off.clear();
     ctx->az_off.clear();
+    ctx->lut_lo.clear();
+    ctx->lut_inv_w.clear();
     for (const SensorHost& s : ctx->sensors) {
         ctx->ch_off.push_back((uint32_t)ch.size());
+        std::vector<float> sins;
         for (double e : s.elev) {
             double sn = std::sin(e), cs = std::cos(e);
             ch.push_back(make_float2((float)sn, (float)cs));
             ch64.push_back(make_double2(sn, cs));
+            sins.push_back((float)sn);
         }
+        float lo, iw;
+        size_t at = lut.size();
+        lut.resize(at + LUT_BINS);
+        build_channel_lut(sins.data(), (uint32_t)sins.size(), lo, iw, lut.data() + at);
+        ctx->lut_lo.push_back(lo);
+        ctx->lut_inv_w.push_back(iw);
         ctx->az_off.push_back((uint32_t)az.size());
         for (uint32_t i = 0; i < s.d.n_rays; ++i) {
             double th = s.d.theta0 + (double)i * s.d.dtheta;
@@ -443,6 +462,10 @@ static grca_status ensure_tables(grca_ctx* ctx, cudaStream_t st) {
     ctx->d_ch64 = nullptr;
     ctx->d_az = nullptr;
     ctx->d_az64 = nullptr;
+    cudaFree(ctx->d_lut);
+    ctx->d_lut = nullptr;
+    CK(cudaMalloc(&ctx->d_lut, sizeof(uint16_t) * std::max<size_t>(lut.size(), 1)));
+    CK(cudaMemcpy(ctx->d_lut, lut.data(), sizeof(uint16_t) * lut.size(), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_ch, sizeof(float2) * std::max<size_t>(ch.size(), 1)));
     CK(cudaMalloc(&ctx->d_ch64, sizeof(double2) * std::max<size_t>(ch.size(), 1)));
     CK(cudaMalloc(&ctx->d_az, sizeof(float2) * std::max<size_t>(az.size(), 1)));
@@ -507,6 +530,9 @@ static void fill_sensor(const grca_ctx* ctx, int id, uint32_t ray_off, SensorDev
     double det = d.f[0] * (d.r[1] * d.u[2] - d.r[2] * d.u[1]) - d.f[1] * (d.r[0] * d.u[2] - d.r[2] * d.u[0]) +
                  d.f[2] * (d.r[0] * d.u[1] - d.r[1] * d.u[0]);
     s.hand = det < 0.0 ? -1.f : 1.f;
+    s.lut_lo = ctx->lut_lo[id];
+    s.lut_inv_w = ctx->lut_inv_w[id];
+    s.lut_off = (uint32_t)id * LUT_BINS;
 }
 
 static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, float* out_dist, uint32_t* out_tri,
@@ -528,6 +554,20 @@ static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, f
     if (total >= 0xFFFFFFFFull || total_ch > 8192) return GRCA_ERR_INVALID_ARG;
     rs = ensure_rays(ctx, total, st);
     if (rs != GRCA_OK) return rs;
+    // survivor queue: one slot per (triangle, sensor) pair, capped by the option
+    {
+        uint64_t need = std::max<uint64_t>((uint64_t)ctx->n_tris * n, 1);
+        need = std::min<uint64_t>(need, ctx->opt.survivor_capacity);
+        if (need > ctx->surv_cap) {
+            CK(cudaStreamSynchronize(st));
+            cudaFree(ctx->d_surv);
+            ctx->d_surv = nullptr;
+            ctx->surv_cap = 0;
+            CK(cudaMalloc(&ctx->d_surv, sizeof(unsigned long long) * need));
+            ctx->surv_cap = need;
+            free_graphs(ctx);
+        }
+    }
     // stage the descriptors through a pinned ring slot (stream-ordered copy)
     int slot = ctx->ring_pos;
     ctx->ring_pos = (ctx->ring_pos + 1) % RING;
@@ -553,6 +593,7 @@ static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, f
     a.ch_sc64 = ctx->d_ch64;
     a.az_sc = ctx->d_az;
     a.az_sc64 = ctx->d_az64;
+    a.lut = ctx->d_lut;
     a.total_ch = (uint32_t)total_ch;
     a.n_rays_total = (uint32_t)total;
     a.keys = ctx->d_keys;
@@ -576,6 +617,8 @@ static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, f
     a.dump_count = ctx->dump_count;
     a.out_dist = out_dist;
     a.out_tri = out_tri;
+    a.surv = ctx->d_surv;
+    a.surv_cap = (uint32_t)ctx->surv_cap;
     return GRCA_OK;
 }
 
@@ -681,6 +724,7 @@ grca_status grca_get_stats(grca_ctx* ctx, grca_stats* out, void* stream) {
     memset(out, 0, sizeof(*out));
     out->pairs = c[C_PAIRS];
     out->pairs_live = c[C_PAIRS_LIVE];
+    out->survivors = c[C_SURV];
     out->candidates = c[C_CAND];
     out->candidates_inline = c[C_CAND_INLINE];
     out->big_pairs = c[C_BIG];

@@ -18,14 +18,14 @@ constexpr int MAX_CHANNELS = 1024;
 constexpr int MAX_RAYS = 32768;
 
 // queue counters (device uint32[8])
-enum { Q_BIG = 0, Q_CHUNK = 1, Q_RECHECK = 2, Q_FLAG = 3, Q_DUMP = 4, Q_NUM = 8 };
+enum { Q_BIG = 0, Q_CHUNK = 1, Q_RECHECK = 2, Q_FLAG = 3, Q_DUMP = 4, Q_SURV = 5, Q_NUM = 8 };
 // statistics counters (device u64[16])
 enum {
     C_PAIRS = 0, C_PAIRS_LIVE, C_CAND, C_CAND_INLINE, C_BIG, C_CHUNKS, C_TESTS, C_HITS,
-    C_UNCERTAIN, C_TIES, C_FLAGGED, C_RECHECK, C_NUM = 16
+    C_UNCERTAIN, C_TIES, C_FLAGGED, C_RECHECK, C_SURV, C_NUM = 16
 };
 // device error bits
-enum { ERR_BIG_CAP = 1, ERR_CHUNK_CAP = 2, ERR_RECHECK_CAP = 4, ERR_FLAG_CAP = 8, ERR_DUMP_CAP = 16 };
+enum { ERR_BIG_CAP = 1, ERR_CHUNK_CAP = 2, ERR_RECHECK_CAP = 4, ERR_FLAG_CAP = 8, ERR_DUMP_CAP = 16, ERR_SURV_CAP = 32 };
 
 // One sensor of a cast, as the kernels read it.  FP64 first (alignment).
 struct SensorDev {
@@ -45,7 +45,32 @@ struct SensorDev {
     uint32_t has_range;   // 1: d_min > 0 or d_max finite
     uint32_t ch_loc;      // offset of this sensor's channels in the cast-local (shared-memory) table
     float hand;           // det([f; r; u]) = +-1: emitter-frame triple products carry this sign
+    float lut_lo;         // channel lookup table: bin b covers sin(elevation) from lut_lo + b / lut_inv_w
+    float lut_inv_w;
+    uint32_t lut_off;     // offset of this sensor's table in the global lookup-table array
+    uint32_t pad_;
 };
+
+// Channel lookup table: LUT_BINS bins over [sin(elev_0) - 0.01, sin(elev_last) + 0.01];
+// bin b stores a channel index no larger than the first channel whose FP32
+// sine is >= any value falling in the bin, so a lookup followed by a short
+// forward scan gives the exact lower/upper bound in the sorted sine table.
+constexpr int LUT_BINS = 512;
+
+inline void build_channel_lut(const float* sins, uint32_t n, float& lo_out, float& inv_w_out, uint16_t* lut) {
+    double lo = (double)sins[0] - 0.01, hi = (double)sins[n - 1] + 0.01;
+    if (lo < -1.0) lo = -1.0;
+    if (hi > 1.0) hi = 1.0;
+    double w = (hi - lo) / LUT_BINS;
+    lo_out = (float)lo;
+    inv_w_out = (float)(1.0 / w);
+    uint32_t j = 0;
+    for (int b = 0; b < LUT_BINS; ++b) {
+        double edge = lo + (b - 0.5) * w;  // half a bin of slack for FP32 rounding of the bin index
+        while (j < n && (double)sins[j] < edge) ++j;
+        lut[b] = (uint16_t)j;
+    }
+}
 
 // Per (triangle, sensor) test setup: everything the per-candidate
 // ray-triangle test needs (emitter frame), 80 bytes.
@@ -87,6 +112,7 @@ struct CastArgs {
     const double2* ch_sc64;
     const float2* az_sc;      // (sin, cos) of ray azimuths, FP32
     const double2* az_sc64;
+    const uint16_t* lut;      // channel lookup tables (LUT_BINS per registered sensor)
     uint32_t total_ch;
     uint32_t n_rays_total;
     unsigned long long* keys;
@@ -112,6 +138,8 @@ struct CastArgs {
     uint32_t* dump_count;
     float* out_dist;
     uint32_t* out_tri;
+    unsigned long long* surv;  // (triangle, sensor, channel span) pairs that pass the elevation cull
+    uint32_t surv_cap;
 };
 
 struct LaunchCfg {
@@ -123,7 +151,7 @@ struct LaunchCfg {
 };
 
 // kernels of one frame, in launch order
-enum { K_INIT = 0, K_CULL, K_EXPAND, K_TEST, K_RECHECK_RAYS, K_RECHECK_PAIRS, K_DECODE, K_NUM };
+enum { K_INIT = 0, K_CULL_A, K_CULL_B, K_EXPAND, K_TEST, K_RECHECK_RAYS, K_RECHECK_PAIRS, K_DECODE, K_NUM };
 extern const char* const kKernelNames[K_NUM];
 
 // optional per-kernel hook: called with phase 0 before and phase 1 after each
@@ -136,6 +164,7 @@ struct KernelMarks {
 // launcher (grca_kernels.cu); returns the number of kernels launched
 int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t st,
                  const KernelMarks* marks = nullptr);
-size_t cull_smem_bytes(const CastArgs& a, const LaunchCfg& cfg);
+size_t cull_smem_bytes(const CastArgs& a, const LaunchCfg& cfg);  // fused k_cull
+// launch the fused culling kernel (allocation-free path)
 
 }  // namespace grca

@@ -27,6 +27,7 @@
 // ray passes between them.  t = ((v0-o).n) / (d.n).
 #include <cooperative_groups.h>
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <cuda_runtime.h>
@@ -123,17 +124,22 @@ __device__ __forceinline__ void make_setup(const SensorDev& S, const TriW& T, co
     // forward hit <=> every emitter-frame edge function has the sign of the
     // emitter-frame triple product p0.(p1 x p2) = det(B) * det
     float fold = (det < 0.f ? -1.f : 1.f) * S.hand;
+    float r2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r2[k] = w[k].x * w[k].x + w[k].y * w[k].y + w[k].z * w[k].z;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         V3 e = rotB(S.B, T.E[k]);
-        V3 pb = p[T.base[k]];
-        V3 m = vcross(pb, e);
+        V3 m = vcross(p[T.base[k]], e);
         float f = T.sg[k] * fold;
         if (f < 0.f) m = vneg(m);
         st.m[3 * k + 0] = m.x;
         st.m[3 * k + 1] = m.y;
         st.m[3 * k + 2] = m.z;
-        st.tau[k] = U32 * (12.f * vnorm(pb) * vnorm(e) + 6.f * vnorm(m)) + 1e-30f;
+        // FP32 error bound of d.m: errors of p_base, e (rotation, origin) and of
+        // the cross and dot products, all <= 18 u |p_base| |e| (|m| <= |p_base| |e|)
+        float ee = T.E[k].x * T.E[k].x + T.E[k].y * T.E[k].y + T.E[k].z * T.E[k].z;
+        st.tau[k] = 18.f * U32 * sqrtf(r2[T.base[k]] * ee) + 1e-30f;
     }
     V3 ne = rotB(S.B, T.n);
     st.n[0] = ne.x;
@@ -142,16 +148,10 @@ __device__ __forceinline__ void make_setup(const SensorDev& S, const TriW& T, co
     st.det = det;
     st.err_det = det != 0.f ? err_det_abs / fabsf(det) : 1.f;
     st.state = unc ? 1u : 0u;
-    float an[3] = {fabsf(T.n.x), fabsf(T.n.y), fabsf(T.n.z)};
-    float aN[3] = {T.N.x, T.N.y, T.N.z};
-    float ane[3] = {fabsf(ne.x), fabsf(ne.y), fabsf(ne.z)};
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        float g = 0.f;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) g += fabsf(S.B[3 * i + k]) * (3.f * an[k] + 3.f * aN[k]);
-        st.G[i] = U32 * (g + 6.f * ane[i]);
-    }
+    float q0 = 3.f * (fabsf(T.n.x) + T.N.x), q1 = 3.f * (fabsf(T.n.y) + T.N.y), q2 = 3.f * (fabsf(T.n.z) + T.N.z);
+    st.G[0] = U32 * (fabsf(S.B[0]) * q0 + fabsf(S.B[1]) * q1 + fabsf(S.B[2]) * q2 + 6.f * fabsf(ne.x));
+    st.G[1] = U32 * (fabsf(S.B[3]) * q0 + fabsf(S.B[4]) * q1 + fabsf(S.B[5]) * q2 + 6.f * fabsf(ne.y));
+    st.G[2] = U32 * (fabsf(S.B[6]) * q0 + fabsf(S.B[7]) * q1 + fabsf(S.B[8]) * q2 + 6.f * fabsf(ne.z));
     st.pad_ = 0.f;
 }
 
@@ -234,7 +234,7 @@ __device__ __forceinline__ void push_recheck(const CastArgs& a, uint32_t g, uint
         atomicOr(a.error, (uint32_t)ERR_RECHECK_CAP);
 }
 
-__device__ __forceinline__ void dump_candidate(const CastArgs& a, uint32_t g, uint32_t tri) {
+__device__ __noinline__ void dump_candidate(const CastArgs& a, uint32_t g, uint32_t tri) {
     uint32_t idx = atomicAdd(a.dump_count, 1u);
     if (idx < a.dump_cap) {
         a.dump[2 * idx] = g;
@@ -343,13 +343,10 @@ __device__ __forceinline__ int upper_bound_sin(const float2* ch, int n, float x)
 // ray-unit coordinate of an absolute azimuth, normalised into one period
 __device__ __forceinline__ float ray_units(const SensorDev& S, float theta) {
     float x = (theta - S.theta0) * S.inv_dtheta;
-    if (S.full) {
-        float n = (float)S.n_rays;
-        x -= n * floorf(x / n);
-    } else {
-        float g0 = -0.5f * (S.period - (float)S.n_rays);
-        x -= S.period * floorf((x - g0) / S.period);
-    }
+    // normalise into one period [g0, g0 + P); P = n_rays for full circles
+    float P = S.full ? (float)S.n_rays : S.period;
+    float g0 = S.full ? 0.f : -0.5f * (S.period - (float)S.n_rays);
+    x -= P * floorf((x - g0) * __frcp_rn(P));
     return x;
 }
 
@@ -430,58 +427,158 @@ __device__ __forceinline__ bool axis_pierces(const V3 p[3]) {
     return (c0 >= -t0 && c1 >= -t1 && c2 >= -t2) || (c0 <= t0 && c1 <= t1 && c2 <= t2);
 }
 
-// Channel span (exact elevation extent, padded) and azimuth span (vertex
-// projections, Sec. 3.7; full circle when the vertical axis pierces the
-// triangle, which the paper covers with its all-CW / seam logic).
-__device__ __forceinline__ bool pair_span(const SensorDev& S, const float2* ch, const V3 p[3], float s_v[3], Span& sp) {
-    float smin = 2.f, smax = -2.f;
+// atan2 by octant reduction and t*P(t^2) on t in [0, 1]; the coefficients
+// are a weighted least-squares fit of atan on [0, 1] made for this file (max
+// error of the FP32 evaluation 3.2e-7 rad, plus the reduction's roundings:
+// callers pad the result by 2e-6 rad)
+constexpr float ATAN_C0 = 0.9999960660934448f, ATAN_C1 = -0.33317309617996216f, ATAN_C2 = 0.19807466864585876f,
+                ATAN_C3 = -0.13232387602329254f, ATAN_C4 = 0.07961045205593109f, ATAN_C5 = -0.03359520062804222f,
+                ATAN_C6 = 0.006809381302446127f;
+constexpr float FAST_ATAN_PAD = 2e-6f;
+
+__device__ __forceinline__ float fast_atan2(float y, float x) {
+    float ax = fabsf(x), ay = fabsf(y);
+    float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    float t = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+    float t2 = t * t;
+    float r = fmaf(t2, ATAN_C6, ATAN_C5);
+    r = fmaf(t2, r, ATAN_C4);
+    r = fmaf(t2, r, ATAN_C3);
+    r = fmaf(t2, r, ATAN_C2);
+    r = fmaf(t2, r, ATAN_C1);
+    r = fmaf(t2, r, ATAN_C0);
+    r *= t;
+    if (ay > ax) r = 1.5707963f - r;
+    if (x < 0.f) r = 3.1415927f - r;
+    return copysignf(r, y);
+}
+
+// first channel j with sin(elev_j) >= x (lower) / > x (upper), via the table
+__device__ __forceinline__ int lut_bin(const SensorDev& S, float x) {
+    float fb = (x - S.lut_lo) * S.lut_inv_w;
+    return fb <= 0.f ? 0 : (fb >= (float)(LUT_BINS - 1) ? LUT_BINS - 1 : (int)fb);
+}
+__device__ __forceinline__ int chan_lower(const SensorDev& S, const float2* ch, const uint16_t* lut, float x) {
+    int j = lut[lut_bin(S, x)], n = (int)S.n_ch;
+    while (j < n && ch[j].x < x) ++j;
+    return j;
+}
+__device__ __forceinline__ int chan_upper(const SensorDev& S, const float2* ch, const uint16_t* lut, float x) {
+    int j = lut[lut_bin(S, x)], n = (int)S.n_ch;
+    while (j < n && ch[j].x <= x) ++j;
+    return j;
+}
+
+// Elevation range (sine) of the triangle's directions.  Vertex values, then
+// per edge: long edges add their interior great-circle extremum; short edges
+// (angular length alpha <= (pi/2)|e|/min(|a|,|b|) < 5e-3) instead widen the
+// range by alpha^2/8, the most a great-circle arc of length alpha rises above
+// its endpoints.  Returns whether the vertical axis meets the triangle.
+__device__ __forceinline__ bool elev_range(const V3 p[3], float& smin, float& smax) {
+    float r2[3], sv[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        float r2 = p[k].x * p[k].x + p[k].y * p[k].y + p[k].z * p[k].z;
-        s_v[k] = r2 > 0.f ? p[k].z * rsqrtf(r2) : 0.f;
-        smin = fminf(smin, s_v[k]);
-        smax = fmaxf(smax, s_v[k]);
+        r2[k] = p[k].x * p[k].x + p[k].y * p[k].y + p[k].z * p[k].z;
+        sv[k] = r2[k] > 0.f ? p[k].z * rsqrtf(r2[k]) : 0.f;
     }
-    edge_elev_extremum(p[0], p[1], smin, smax);
-    edge_elev_extremum(p[1], p[2], smin, smax);
-    edge_elev_extremum(p[2], p[0], smin, smax);
+    smin = fminf(sv[0], fminf(sv[1], sv[2]));
+    smax = fmaxf(sv[0], fmaxf(sv[1], sv[2]));
+    float dev = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int k1 = k == 2 ? 0 : k + 1;
+        V3 a = p[k], b = p[k1];
+        float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
+        float ee = ex * ex + ey * ey + ez * ez;
+        float m2 = fminf(r2[k], r2[k1]);
+        if (ee < 1e-5f * m2)
+            dev = fmaxf(dev, 0.31f * ee * __frcp_ru(m2));
+        else
+            edge_elev_extremum(a, b, smin, smax);
+    }
+    smin -= dev;
+    smax += dev;
     bool pierced = axis_pierces(p);
     if (pierced) {
         if (fmaxf(p[0].z, fmaxf(p[1].z, p[2].z)) > 0.f) smax = 1.f;
         if (fminf(p[0].z, fminf(p[1].z, p[2].z)) < 0.f) smin = -1.f;
     }
-    int n_ch = (int)S.n_ch;
-    int jl = lower_bound_sin(ch, n_ch, smin - EPS_S);
-    int jh = upper_bound_sin(ch, n_ch, smax + EPS_S) - 1;
-    if (jl > jh) return false;
-    sp.j_lo = jl;
-    sp.j_hi = jh;
-    sp.pierced = pierced;
-    float th0 = atan2f(p[0].y, p[0].x);
-    sp.a0 = ray_units(S, th0);
-    float A, B;
-    if (pierced) {
-        A = sp.a0 - 0.5f * S.period;
-        B = sp.a0 + 0.5f * S.period;
-        if (S.full) {
-            sp.u_lo = 0;
-            sp.n_r = (int)S.n_rays;
-            return true;
-        }
-    } else {
-        float d1 = rel_angle(p[0], p[1]);
-        float d2 = rel_angle(p[0], p[2]);
-        float pad = EPS_T + az_pad_s(s_v[0]) + az_pad_s(s_v[1]) + az_pad_s(s_v[2]);
-        float lo = fminf(0.f, fminf(d1, d2)) - pad, hi = fmaxf(0.f, fmaxf(d1, d2)) + pad;
-        if (hi - lo >= 6.2831f) {
-            A = sp.a0 - 0.5f * S.period;
-            B = sp.a0 + 0.5f * S.period;
+    return pierced;
+}
+
+// World-frame (rotation-free) elevation range for phase A: only z = u.w and
+// |w|^2 per vertex are needed, both invariant under the emitter rotation.
+// Same bounds as elev_range; the vertical-axis test runs in the emitter frame
+// only when a necessary condition holds: the projected triangle can contain
+// the origin only if its nearest vertex lies within the longest edge of it.
+__device__ __forceinline__ bool elev_range_w(const SensorDev& S, const V3 w[3], float& smin, float& smax) {
+    const V3 u = {S.B[6], S.B[7], S.B[8]};
+    float z[3], r2[3], sv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        z[k] = u.x * w[k].x + u.y * w[k].y + u.z * w[k].z;
+        r2[k] = w[k].x * w[k].x + w[k].y * w[k].y + w[k].z * w[k].z;
+        sv[k] = r2[k] > 0.f ? z[k] * rsqrtf(r2[k]) : 0.f;
+    }
+    smin = fminf(sv[0], fminf(sv[1], sv[2]));
+    smax = fmaxf(sv[0], fmaxf(sv[1], sv[2]));
+    float dev = 0.f, ee_max = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int k1 = k == 2 ? 0 : k + 1;
+        V3 a = w[k];
+        V3 e = {w[k1].x - a.x, w[k1].y - a.y, w[k1].z - a.z};
+        float ee = e.x * e.x + e.y * e.y + e.z * e.z;
+        ee_max = fmaxf(ee_max, ee);
+        float m2 = fminf(r2[k], r2[k1]);
+        if (ee < 1e-5f * m2) {
+            dev = fmaxf(dev, 0.31f * ee * __frcp_ru(m2));
         } else {
-            A = sp.a0 + lo * S.inv_dtheta;
-            B = sp.a0 + hi * S.inv_dtheta;
+            // interior extremum of the edge's great circle: +-|m_h|/|m|, m = a x e
+            float ez = z[k1] - z[k];
+            float ae = a.x * e.x + a.y * e.y + a.z * e.z;
+            float num = z[k] * ae - ez * r2[k];
+            float den = ez * ae - z[k] * ee;
+            if (den < 0.f) {
+                num = -num;
+                den = -den;
+            }
+            if (den > 0.f && num > -1e-3f * den && num < 1.001f * den) {
+                V3 m = {a.y * e.z - a.z * e.y, a.z * e.x - a.x * e.z, a.x * e.y - a.y * e.x};
+                float mm = m.x * m.x + m.y * m.y + m.z * m.z;
+                float mz = u.x * m.x + u.y * m.y + u.z * m.z;
+                if (mm > 1e-12f * r2[k] * ee) {
+                    float v = sqrtf(fmaxf(mm - mz * mz, 0.f) * __frcp_rn(mm));
+                    float lam = fminf(fmaxf(num / den, 0.f), 1.f);
+                    float qz = z[k] + lam * ez;
+                    float tol = 1e-4f * sqrtf(r2[k] + ee);
+                    if (qz >= -tol) smax = fmaxf(smax, v);
+                    if (qz <= tol) smin = fminf(smin, -v);
+                }
+            }
         }
     }
-    return ray_interval(S, A - PADR, B + PADR, sp.u_lo, sp.n_r);
+    smin -= dev;
+    smax += dev;
+    float h2min = fminf(r2[0] - z[0] * z[0], fminf(r2[1] - z[1] * z[1], r2[2] - z[2] * z[2]));
+    float r2max = fmaxf(r2[0], fmaxf(r2[1], r2[2]));
+    bool pierced = false;
+    if (h2min <= 1.01f * ee_max + 8.f * U32 * r2max) {
+        V3 p[3] = {rotB(S.B, w[0]), rotB(S.B, w[1]), rotB(S.B, w[2])};
+        pierced = axis_pierces(p);
+    }
+    if (pierced) {
+        if (fmaxf(z[0], fmaxf(z[1], z[2])) > 0.f) smax = 1.f;
+        if (fminf(z[0], fminf(z[1], z[2])) < 0.f) smin = -1.f;
+    }
+    return pierced;
+}
+
+// azimuth padding of vertex p from |p|^2 and |p_h|^2
+__device__ __forceinline__ float az_pad2(V3 p) {
+    float h2 = p.x * p.x + p.y * p.y;
+    float r2 = h2 + p.z * p.z;
+    return h2 > 1e-12f * r2 ? 16.f * U32 * r2 * rsqrtf(r2 * h2) : 10.f;
 }
 
 // closest-point distance from the origin to the triangle (w = vertices
@@ -542,135 +639,519 @@ __device__ __forceinline__ void warp_add(unsigned long long* ctr, uint32_t v) {
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(ctr, (unsigned long long)s);
 }
 
+// ---------------------------------------------------------------------------
+// culling, shared by the fused kernel (k_cull) and the split pair (k_cull_a,
+// k_cull_b)
+// ---------------------------------------------------------------------------
+struct CullCounters {
+    uint32_t live = 0, cand = 0, inl = 0, big = 0, tests = 0, hits = 0, unc = 0, ties = 0;
+    __device__ void flush(const CastArgs& a) const {
+        warp_add(&a.counters[C_PAIRS_LIVE], live);
+        warp_add(&a.counters[C_CAND], cand);
+        warp_add(&a.counters[C_CAND_INLINE], inl);
+        warp_add(&a.counters[C_BIG], big);
+        warp_add(&a.counters[C_TESTS], tests);
+        warp_add(&a.counters[C_HITS], hits);
+        warp_add(&a.counters[C_UNCERTAIN], unc);
+        warp_add(&a.counters[C_TIES], ties);
+    }
+};
+
+// channel span bits: j_lo | j_hi << 10 | pierced << 20  (channels < 1024)
+__device__ __forceinline__ uint32_t pack_span(int jl, int jh, bool pierced) {
+    return (uint32_t)jl | ((uint32_t)jh << 10) | (pierced ? (1u << 20) : 0u);
+}
+
+// Phase A of one (triangle, sensor) pair: back-face cull (if requested) and
+// the channel span from the elevation range.  Returns false when culled.
+template <bool RECHECK, bool BRUTE>
+__device__ __forceinline__ bool cull_elevation(const SensorDev& S, const float2* ch, const uint16_t* lut, const V3 v[3],
+                                               const V3& nw, bool cull_back, uint32_t& span) {
+    V3 w0 = rel_origin(S, v[0]);
+    if (cull_back) {
+        float det = vdot(w0, nw);
+        V3 e1 = vsub(v[1], v[0]), e2 = vsub(v[2], v[0]);
+        float Nx = fabsf(e1.y * e2.z) + fabsf(e1.z * e2.y), Ny = fabsf(e1.z * e2.x) + fabsf(e1.x * e2.z),
+              Nz = fabsf(e1.x * e2.y) + fabsf(e1.y * e2.x);
+        float err = U32 * (fabsf(w0.x) * (3.f * Nx + 4.f * fabsf(nw.x)) + fabsf(w0.y) * (3.f * Ny + 4.f * fabsf(nw.y)) +
+                           fabsf(w0.z) * (3.f * Nz + 4.f * fabsf(nw.z)));
+        if (det > 0.f && (!RECHECK || det > err)) return false;  // facing <=> det < 0
+    }
+    if (BRUTE) {
+        span = pack_span(0, (int)S.n_ch - 1, false);
+        return true;
+    }
+    const V3 wv[3] = {w0, rel_origin(S, v[1]), rel_origin(S, v[2])};
+    float smin, smax;
+    bool pierced = elev_range_w(S, wv, smin, smax);
+    int jl = chan_lower(S, ch, lut, smin - EPS_S);
+    if (jl >= (int)S.n_ch || ch[jl].x > smax + EPS_S) return false;  // no channel in the range
+    int jh = chan_upper(S, ch, lut, smax + EPS_S) - 1;
+    span = pack_span(jl, jh, pierced);
+    return true;
+}
+
+// Phase B of a surviving pair: range cull, azimuth span, then inline tests or
+// a deferred-queue append.
+template <bool RECHECK, bool BRUTE>
+__device__ __forceinline__ void cull_rest(const CastArgs& a, const SensorDev& S, uint32_t sn, const float2* chs,
+                                          uint32_t tri, const float* t9, uint32_t span, CullCounters& c) {
+    const bool dump = a.flags & 16u;
+    V3 vv[3] = {{t9[0], t9[1], t9[2]}, {t9[3], t9[4], t9[5]}, {t9[6], t9[7], t9[8]}};
+    V3 w[3], p[3];
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+        w[kk] = rel_origin(S, vv[kk]);
+        p[kk] = rotB(S.B, w[kk]);
+    }
+    if (!BRUTE && S.has_range) {
+        // range cull (App. A.4.1 Step 1), only where provably empty
+        float dmax = fmaxf(vnorm(w[0]), fmaxf(vnorm(w[1]), vnorm(w[2])));
+        if (dmax < S.d_min * (1.f - 1e-5f) - 1e-6f) return;
+        if (S.d_max < INFINITY && closest_dist(w[0], w[1], w[2]) > S.d_max * (1.f + 1e-5f) + 1e-6f) return;
+    }
+    Span sp;
+    sp.j_lo = (int)(span & 1023u);
+    sp.j_hi = (int)((span >> 10) & 1023u);
+    sp.pierced = (span >> 20) & 1u;
+    if (BRUTE) {
+        sp.u_lo = 0;
+        sp.n_r = (int)S.n_rays;
+        sp.a0 = 0.f;
+    } else {
+        sp.a0 = ray_units(S, fast_atan2(p[0].y, p[0].x));
+        float A, B;
+        if (sp.pierced) {
+            A = sp.a0 - 0.5f * S.period;
+            B = sp.a0 + 0.5f * S.period;
+        } else {
+            float d1 = rel_angle(p[0], p[1]);
+            float d2 = rel_angle(p[0], p[2]);
+            float pad = EPS_T + FAST_ATAN_PAD + az_pad2(p[0]) + az_pad2(p[1]) + az_pad2(p[2]);
+            float lo = fminf(0.f, fminf(d1, d2)) - pad, hi = fmaxf(0.f, fmaxf(d1, d2)) + pad;
+            if (hi - lo >= 6.2831f) {
+                A = sp.a0 - 0.5f * S.period;
+                B = sp.a0 + 0.5f * S.period;
+            } else {
+                A = sp.a0 + lo * S.inv_dtheta;
+                B = sp.a0 + hi * S.inv_dtheta;
+            }
+        }
+        if (!ray_interval(S, A - PADR, B + PADR, sp.u_lo, sp.n_r)) return;
+    }
+    const uint32_t ncand = (uint32_t)(sp.j_hi - sp.j_lo + 1) * (uint32_t)sp.n_r;
+    c.live++;
+    c.cand += ncand;
+    if (!BRUTE && ncand > a.inline_max) {
+        // deferred list append: one atomic per coalesced group (ballot + popc rank)
+        cg::coalesced_group grp = cg::coalesced_threads();
+        uint32_t b0 = 0;
+        if (grp.thread_rank() == 0) b0 = atomicAdd(&a.qcount[Q_BIG], grp.size());
+        b0 = grp.shfl(b0, 0) + grp.thread_rank();
+        if (b0 < a.big_cap) {
+            BigPair bp;
+            bp.tri = tri;
+            bp.sensor = (uint16_t)sn;
+            bp.flags = sp.pierced ? 1 : 0;
+            bp.j_lo = (uint16_t)sp.j_lo;
+            bp.j_hi = (uint16_t)sp.j_hi;
+            bp.u_lo = sp.u_lo;
+            bp.n_r = (uint32_t)sp.n_r;
+            bp.a0 = sp.a0;
+            bp.pad_[0] = bp.pad_[1] = 0;
+            a.big[b0] = bp;
+        } else {
+            atomicOr(a.error, (uint32_t)ERR_BIG_CAP);
+        }
+        c.big++;
+        return;
+    }
+    TriW T;
+    tri_world(t9, T);
+    float det = vdot(w[0], T.n);
+    float err_det = det_error(w[0], T);
+    bool det_unc = fabsf(det) <= err_det;
+    if (det == 0.f && !(RECHECK && det_unc)) return;  // origin in the plane: t = 0, never a hit
+    c.inl += ncand;
+    PairSetup st;
+    make_setup(S, T, w, p, det, err_det, st);
+    const float2* azs = a.az_sc + S.az_off;
+    const int n = (int)S.n_rays;
+    const int r0 = imod(sp.u_lo, n);
+    for (int j = sp.j_lo; j <= sp.j_hi; ++j) {
+        const float2 chv = chs[j];
+        const uint32_t gbase = S.ray_off + (uint32_t)j * (uint32_t)n;
+        int i = r0;
+        for (int qq = 0; qq < sp.n_r; ++qq) {
+            V3 d = ray_dir(chv, __ldg(&azs[i]));
+            float t, terr;
+            int res = test_fp32<RECHECK>(st, S, d, t, terr);
+            c.tests++;
+            if (dump) dump_candidate(a, gbase + i, tri);
+            c.hits += commit<RECHECK>(a, gbase + i, tri, res, t, terr, c.unc, c.ties);
+            if (++i == n) i = 0;
+        }
+    }
+}
+
+// shared-memory prologue: sensor descriptors, channel tables, lookup tables
+struct CullSmem {
+    SensorDev* sens;
+    float2* ch;
+    uint16_t* lut;
+    unsigned char* rest;  // 16-B aligned
+};
+__device__ __forceinline__ CullSmem cull_smem_prologue(const CastArgs& a, unsigned char* smem, bool with_lut) {
+    CullSmem m;
+    m.sens = reinterpret_cast<SensorDev*>(smem);
+    m.ch = reinterpret_cast<float2*>(smem + sizeof(SensorDev) * a.n_sensors);
+    m.lut = reinterpret_cast<uint16_t*>(smem + sizeof(SensorDev) * a.n_sensors + sizeof(float2) * a.total_ch);
+    size_t off = sizeof(SensorDev) * a.n_sensors + sizeof(float2) * a.total_ch +
+                 (with_lut ? sizeof(uint16_t) * LUT_BINS * a.n_sensors : 0);
+    off = (off + 15) & ~size_t(15);
+    m.rest = smem + off;
+    for (uint32_t q = threadIdx.x; q < a.n_sensors * (uint32_t)(sizeof(SensorDev) / 4); q += blockDim.x)
+        reinterpret_cast<uint32_t*>(m.sens)[q] = reinterpret_cast<const uint32_t*>(a.sensors)[q];
+    __syncthreads();
+    for (uint32_t sn = 0; sn < a.n_sensors; ++sn) {
+        const SensorDev& S = m.sens[sn];
+        for (uint32_t j = threadIdx.x; j < S.n_ch; j += blockDim.x) m.ch[S.ch_loc + j] = a.ch_sc[S.ch_off + j];
+        if (with_lut)
+            for (uint32_t b = threadIdx.x; b < LUT_BINS; b += blockDim.x) m.lut[sn * LUT_BINS + b] = a.lut[S.lut_off + b];
+    }
+    __syncthreads();
+    return m;
+}
+
+// stage a warp's 32 triangles (1152 B, 16-B aligned since base % 4 == 0)
+__device__ __forceinline__ void stage_tris(const CastArgs& a, uint32_t base, uint32_t cnt, float* dst, uint32_t lane) {
+    const float4* src = reinterpret_cast<const float4*>(a.tris + 9ull * base);
+    const uint32_t n4 = (cnt * 9u + 3u) >> 2;
+    __syncwarp();
+    for (uint32_t q = lane; q < n4; q += 32) reinterpret_cast<float4*>(dst)[q] = __ldcs(src + q);
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// k_cull (fused): phase A, warp compaction of the survivors, phase B
+// ---------------------------------------------------------------------------
+constexpr int CULL_GROUP = 8;  // sensors per elevation phase
+struct CullWarpSmem {
+    float tri[32 * 9 + 4];            // staged triangles (+ one float4 of slack)
+    uint32_t span[32 * CULL_GROUP];   // channel span per (lane, sensor)
+    uint16_t list[32 * CULL_GROUP];   // surviving (lane, sensor) pairs: lane | k << 5
+};
+static_assert(sizeof(CullWarpSmem) % 16 == 0, "per-warp staging must stay 16-byte aligned");
+
 template <bool RECHECK, bool BRUTE>
 __global__ void __launch_bounds__(256, 3) k_cull(CastArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    SensorDev* s_sens = reinterpret_cast<SensorDev*>(smem);
-    float2* s_ch = reinterpret_cast<float2*>(smem + sizeof(SensorDev) * a.n_sensors);
-    size_t off = sizeof(SensorDev) * a.n_sensors + sizeof(float2) * a.total_ch;
-    off = (off + 15) & ~size_t(15);
+    CullSmem M = cull_smem_prologue(a, smem, true);
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
-    // warp-private staging slice: 32 triangles x 9 floats (+1 float4 of slack)
-    float* s_tri = reinterpret_cast<float*>(smem + off) + wib * (32 * 9 + 4);
-
-    for (uint32_t q = threadIdx.x; q < a.n_sensors * (uint32_t)(sizeof(SensorDev) / 4); q += blockDim.x)
-        reinterpret_cast<uint32_t*>(s_sens)[q] = reinterpret_cast<const uint32_t*>(a.sensors)[q];
-    __syncthreads();
-    for (uint32_t sn = 0; sn < a.n_sensors; ++sn) {
-        const SensorDev& S = s_sens[sn];
-        for (uint32_t j = threadIdx.x; j < S.n_ch; j += blockDim.x) s_ch[S.ch_loc + j] = a.ch_sc[S.ch_off + j];
-    }
-    __syncthreads();
-
+    CullWarpSmem& W = reinterpret_cast<CullWarpSmem*>(M.rest)[wib];
     const bool cull_back = a.flags & 2u;
-    const bool dump = a.flags & 16u;
-    uint32_t c_live = 0, c_cand = 0, c_inl = 0, c_big = 0, c_tests = 0, c_hits = 0, c_unc = 0, c_ties = 0;
-
+    CullCounters c;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t gwarp = ((blockIdx.x * blockDim.x) >> 5) + wib;
     for (uint32_t base = gwarp * 32; base < a.n_tris; base += n_warps * 32) {
-        uint32_t cnt = min(32u, a.n_tris - base);
-        // a warp's 32 triangles are 1152 B, 16-B aligned (base % 4 == 0)
-        const float4* src = reinterpret_cast<const float4*>(a.tris + 9ull * base);
-        uint32_t n4 = (cnt * 9u + 3u) >> 2;
-        __syncwarp();
-        for (uint32_t q = lane; q < n4; q += 32) reinterpret_cast<float4*>(s_tri)[q] = __ldcs(src + q);
-        __syncwarp();
-        if (lane >= cnt) continue;
-        const uint32_t tri = base + lane;
-        TriW T;
-        tri_world(s_tri + 9 * lane, T);
-        if (T.n.x == 0.f && T.n.y == 0.f && T.n.z == 0.f) continue;  // zero area: never hit
+        const uint32_t cnt = min(32u, a.n_tris - base);
+        stage_tris(a, base, cnt, W.tri, lane);
+        bool valid = lane < cnt;
+        const float* t9 = W.tri + 9 * (valid ? lane : 0);
+        V3 v[3] = {{t9[0], t9[1], t9[2]}, {t9[3], t9[4], t9[5]}, {t9[6], t9[7], t9[8]}};
+        V3 nw = vcross(vsub(v[1], v[0]), vsub(v[2], v[0]));
+        if (nw.x == 0.f && nw.y == 0.f && nw.z == 0.f) valid = false;  // zero area: never hit
+        for (uint32_t sg = 0; sg < a.n_sensors; sg += CULL_GROUP) {
+            const uint32_t ng = min((uint32_t)CULL_GROUP, a.n_sensors - sg);
+            uint32_t mask = 0;
+            if (valid) {
+                for (uint32_t k = 0; k < ng; ++k) {
+                    uint32_t span;
+                    if (cull_elevation<RECHECK, BRUTE>(M.sens[sg + k], M.ch + M.sens[sg + k].ch_loc,
+                                                       M.lut + (sg + k) * LUT_BINS, v, nw, cull_back, span)) {
+                        mask |= 1u << k;
+                        W.span[lane * CULL_GROUP + k] = span;
+                    }
+                }
+            }
+            const uint32_t my = __popc(mask);
+            uint32_t incl = my;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)lane >= o) incl += t;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            {
+                uint32_t at = incl - my, m = mask;
+                while (m) {
+                    uint32_t k = __ffs(m) - 1;
+                    m &= m - 1;
+                    W.list[at++] = (uint16_t)(lane | (k << 5));
+                }
+            }
+            __syncwarp();
+            for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                if (q < total) {
+                    const uint32_t e = W.list[q];
+                    const uint32_t srcl = e & 31u, k = e >> 5, sn = sg + k;
+                    cull_rest<RECHECK, BRUTE>(a, M.sens[sn], sn, M.ch + M.sens[sn].ch_loc, base + srcl,
+                                              W.tri + 9 * srcl, W.span[srcl * CULL_GROUP + k], c);
+                }
+            }
+            __syncwarp();
+        }
+    }
+    c.flush(a);
+}
 
-        for (uint32_t sn = 0; sn < a.n_sensors; ++sn) {
-            const SensorDev& S = s_sens[sn];
+// ---------------------------------------------------------------------------
+// k_cull_a: phase A over all pairs; survivors go to a global queue through a
+// per-warp shared-memory buffer (one atomic per flush of >= 256 entries)
+// record: tri | span << 32 | sensor << 53
+// ---------------------------------------------------------------------------
+constexpr int SURV_BUF = 384;  // >= 32 * CULL_GROUP + some slack
+struct CullAWarpSmem {
+    float tri[32 * 9 + 4];
+    unsigned long long buf[SURV_BUF];
+};
+static_assert(sizeof(CullAWarpSmem) % 16 == 0, "per-warp staging must stay 16-byte aligned");
+
+__device__ __forceinline__ void flush_survivors(const CastArgs& a, CullAWarpSmem& W, uint32_t& fill, uint32_t lane) {
+    uint32_t b0 = 0;
+    if (lane == 0 && fill) b0 = atomicAdd(&a.qcount[Q_SURV], fill);
+    b0 = __shfl_sync(0xffffffffu, b0, 0);
+    for (uint32_t q = lane; q < fill; q += 32) {
+        if (b0 + q < a.surv_cap)
+            a.surv[b0 + q] = W.buf[q];
+        else
+            atomicOr(a.error, (uint32_t)ERR_SURV_CAP);
+    }
+    __syncwarp();
+    fill = 0;
+}
+
+template <bool RECHECK, bool BRUTE>
+__global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    CullSmem M = cull_smem_prologue(a, smem, true);
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    CullAWarpSmem& W = reinterpret_cast<CullAWarpSmem*>(M.rest)[wib];
+    const bool cull_back = a.flags & 2u;
+    uint32_t fill = 0;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t gwarp = ((blockIdx.x * blockDim.x) >> 5) + wib;
+    for (uint32_t base = gwarp * 32; base < a.n_tris; base += n_warps * 32) {
+        const uint32_t cnt = min(32u, a.n_tris - base);
+        stage_tris(a, base, cnt, W.tri, lane);
+        bool valid = lane < cnt;
+        const float* t9 = W.tri + 9 * (valid ? lane : 0);
+        V3 v[3] = {{t9[0], t9[1], t9[2]}, {t9[3], t9[4], t9[5]}, {t9[6], t9[7], t9[8]}};
+        V3 nw = vcross(vsub(v[1], v[0]), vsub(v[2], v[0]));
+        if (nw.x == 0.f && nw.y == 0.f && nw.z == 0.f) valid = false;  // zero area: never hit
+        for (uint32_t sg = 0; sg < a.n_sensors; sg += CULL_GROUP) {
+            const uint32_t ng = min((uint32_t)CULL_GROUP, a.n_sensors - sg);
+            if (fill + 32 * CULL_GROUP > SURV_BUF) flush_survivors(a, W, fill, lane);
+            for (uint32_t k = 0; k < ng; ++k) {
+                uint32_t span = 0;
+                bool ok = valid && cull_elevation<RECHECK, BRUTE>(M.sens[sg + k], M.ch + M.sens[sg + k].ch_loc,
+                                                                  M.lut + (sg + k) * LUT_BINS, v, nw, cull_back, span);
+                uint32_t bal = __ballot_sync(0xffffffffu, ok);
+                if (ok)
+                    W.buf[fill + __popc(bal & ((1u << lane) - 1u))] =
+                        (unsigned long long)(base + lane) | ((unsigned long long)span << 32) |
+                        ((unsigned long long)(sg + k) << 53);
+                fill += __popc(bal);
+            }
+            __syncwarp();
+        }
+    }
+    flush_survivors(a, W, fill, lane);
+}
+
+// ---------------------------------------------------------------------------
+// k_cull_b: phase B over the survivor queue, warp-cooperative.  Each warp
+// takes 32 survivors: (1) per lane, range cull and azimuth span; large spans
+// go to the deferred queue; (2) per lane with a small live span, the test
+// setup into shared memory; (3) the warp expands all candidates of its 32
+// pairs together, one candidate per lane (owner found by binary search over
+// the warp's prefix sums), so the tests run without lane divergence.
+// ---------------------------------------------------------------------------
+struct CullBWarpSmem {
+    PairSetup st[32];
+    uint32_t incl[32];    // inclusive prefix of candidate counts
+    uint32_t tri[32];
+    uint32_t meta[32];    // j_lo | n_r << 10 | sensor << 26
+    uint32_t r0[32];
+    float inv_nr[32];     // 1 / n_r (rounded up), for the candidate -> (channel, ray) split
+};
+
+template <bool RECHECK, bool BRUTE>
+__global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    CullSmem M = cull_smem_prologue(a, smem, false);
+    const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    CullBWarpSmem& W = reinterpret_cast<CullBWarpSmem*>(M.rest)[wib];
+    const bool dump = a.flags & 16u;
+    CullCounters c;
+    const uint32_t n = min(*(volatile uint32_t*)&a.qcount[Q_SURV], a.surv_cap);
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t gwarp = ((blockIdx.x * blockDim.x) >> 5) + wib;
+    for (uint32_t b0 = gwarp * 32; b0 < n; b0 += n_warps * 32) {
+        const uint32_t q = b0 + lane;
+        uint32_t ncand = 0;
+        if (q < n) {
+            const unsigned long long r = __ldcs(&a.surv[q]);
+            const uint32_t tri = (uint32_t)r, span = (uint32_t)(r >> 32) & 0x1FFFFFu, sn = (uint32_t)(r >> 53);
+            const SensorDev& S = M.sens[sn];
+            float t9[9];
+            const float* src = a.tris + 9ull * tri;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) t9[k] = __ldg(src + k);
+            V3 vv[3] = {{t9[0], t9[1], t9[2]}, {t9[3], t9[4], t9[5]}, {t9[6], t9[7], t9[8]}};
             V3 w[3], p[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                w[k] = rel_origin(S, T.v[k]);
-                p[k] = rotB(S.B, w[k]);
+            for (int kk = 0; kk < 3; ++kk) {
+                w[kk] = rel_origin(S, vv[kk]);
+                p[kk] = rotB(S.B, w[kk]);
             }
-            float det = vdot(w[0], T.n);
-            float err_det = det_error(w[0], T);
-            bool det_unc = fabsf(det) <= err_det;
-            if (!RECHECK && det == 0.f) continue;        // origin in the plane: t = 0, never a hit
-            if (RECHECK && det == 0.f && !det_unc) continue;
-            if (cull_back && det > 0.f && (!RECHECK || !det_unc)) continue;   // facing <=> det < 0
+            bool keep = true;
             if (!BRUTE && S.has_range) {
-                float dmin = closest_dist(w[0], w[1], w[2]);
+                // range cull (App. A.4.1 Step 1), only where provably empty
                 float dmax = fmaxf(vnorm(w[0]), fmaxf(vnorm(w[1]), vnorm(w[2])));
-                if (dmin > S.d_max * (1.f + 1e-5f) + 1e-6f) continue;
-                if (dmax < S.d_min * (1.f - 1e-5f) - 1e-6f) continue;
+                if (dmax < S.d_min * (1.f - 1e-5f) - 1e-6f) keep = false;
+                if (keep && S.d_max < INFINITY && closest_dist(w[0], w[1], w[2]) > S.d_max * (1.f + 1e-5f) + 1e-6f)
+                    keep = false;
             }
             Span sp;
-            float s_v[3];
-            if (BRUTE) {
-                sp.j_lo = 0;
-                sp.j_hi = (int)S.n_ch - 1;
-                sp.u_lo = 0;
-                sp.n_r = (int)S.n_rays;
-            } else if (!pair_span(S, s_ch + S.ch_loc, p, s_v, sp)) {
-                continue;
-            }
-            uint32_t ncand = (uint32_t)(sp.j_hi - sp.j_lo + 1) * (uint32_t)sp.n_r;
-            c_live++;
-            c_cand += ncand;
-            if (!BRUTE && ncand > a.inline_max) {
-                // deferred list append: one atomic per coalesced group (ballot + popc rank)
-                cg::coalesced_group grp = cg::coalesced_threads();
-                uint32_t b0 = 0;
-                if (grp.thread_rank() == 0) b0 = atomicAdd(&a.qcount[Q_BIG], grp.size());
-                b0 = grp.shfl(b0, 0) + grp.thread_rank();
-                if (b0 < a.big_cap) {
-                    BigPair bp;
-                    bp.tri = tri;
-                    bp.sensor = (uint16_t)sn;
-                    bp.flags = sp.pierced ? 1 : 0;
-                    bp.j_lo = (uint16_t)sp.j_lo;
-                    bp.j_hi = (uint16_t)sp.j_hi;
-                    bp.u_lo = sp.u_lo;
-                    bp.n_r = (uint32_t)sp.n_r;
-                    bp.a0 = sp.a0;
-                    bp.pad_[0] = bp.pad_[1] = 0;
-                    a.big[b0] = bp;
+            sp.j_lo = (int)(span & 1023u);
+            sp.j_hi = (int)((span >> 10) & 1023u);
+            sp.pierced = (span >> 20) & 1u;
+            if (keep) {
+                if (BRUTE) {
+                    sp.u_lo = 0;
+                    sp.n_r = (int)S.n_rays;
+                    sp.a0 = 0.f;
                 } else {
-                    atomicOr(a.error, (uint32_t)ERR_BIG_CAP);
+                    sp.a0 = ray_units(S, fast_atan2(p[0].y, p[0].x));
+                    float A, B;
+                    if (sp.pierced) {
+                        A = sp.a0 - 0.5f * S.period;
+                        B = sp.a0 + 0.5f * S.period;
+                    } else {
+                        float d1 = rel_angle(p[0], p[1]);
+                        float d2 = rel_angle(p[0], p[2]);
+                        float pad = EPS_T + FAST_ATAN_PAD + az_pad2(p[0]) + az_pad2(p[1]) + az_pad2(p[2]);
+                        float lo = fminf(0.f, fminf(d1, d2)) - pad, hi = fmaxf(0.f, fmaxf(d1, d2)) + pad;
+                        if (hi - lo >= 6.2831f) {
+                            A = sp.a0 - 0.5f * S.period;
+                            B = sp.a0 + 0.5f * S.period;
+                        } else {
+                            A = sp.a0 + lo * S.inv_dtheta;
+                            B = sp.a0 + hi * S.inv_dtheta;
+                        }
+                    }
+                    keep = ray_interval(S, A - PADR, B + PADR, sp.u_lo, sp.n_r);
                 }
-                c_big++;
-                continue;
             }
-            c_inl += ncand;
-            PairSetup st;
-            make_setup(S, T, w, p, det, err_det, st);
-            const float2* chs = s_ch + S.ch_loc;
-            const float2* azs = a.az_sc + S.az_off;
-            const int n = (int)S.n_rays;
-            int r0 = imod(sp.u_lo, n);
-            for (int j = sp.j_lo; j <= sp.j_hi; ++j) {
-                float2 chv = chs[j];
-                uint32_t gbase = S.ray_off + (uint32_t)j * (uint32_t)n;
-                int i = r0;
-                for (int q = 0; q < sp.n_r; ++q) {
-                    V3 d = ray_dir(chv, __ldg(&azs[i]));
-                    float t, terr;
-                    int res = test_fp32<RECHECK>(st, S, d, t, terr);
-                    c_tests++;
-                    if (dump) dump_candidate(a, gbase + i, tri);
-                    c_hits += commit<RECHECK>(a, gbase + i, tri, res, t, terr, c_unc, c_ties);
-                    if (++i == n) i = 0;
+            if (keep) {
+                const uint32_t nc = (uint32_t)(sp.j_hi - sp.j_lo + 1) * (uint32_t)sp.n_r;
+                c.live++;
+                c.cand += nc;
+                if (!BRUTE && nc > a.inline_max) {
+                    cg::coalesced_group grp = cg::coalesced_threads();
+                    uint32_t bb = 0;
+                    if (grp.thread_rank() == 0) bb = atomicAdd(&a.qcount[Q_BIG], grp.size());
+                    bb = grp.shfl(bb, 0) + grp.thread_rank();
+                    if (bb < a.big_cap) {
+                        BigPair bp;
+                        bp.tri = tri;
+                        bp.sensor = (uint16_t)sn;
+                        bp.flags = sp.pierced ? 1 : 0;
+                        bp.j_lo = (uint16_t)sp.j_lo;
+                        bp.j_hi = (uint16_t)sp.j_hi;
+                        bp.u_lo = sp.u_lo;
+                        bp.n_r = (uint32_t)sp.n_r;
+                        bp.a0 = sp.a0;
+                        bp.pad_[0] = bp.pad_[1] = 0;
+                        a.big[bb] = bp;
+                    } else {
+                        atomicOr(a.error, (uint32_t)ERR_BIG_CAP);
+                    }
+                    c.big++;
+                } else {
+                    TriW T;
+                    tri_world(t9, T);
+                    float det = vdot(w[0], T.n);
+                    float err_det = det_error(w[0], T);
+                    bool det_unc = fabsf(det) <= err_det;
+                    if (det != 0.f || (RECHECK && det_unc)) {
+                        make_setup(S, T, w, p, det, err_det, W.st[lane]);
+                        W.tri[lane] = tri;
+                        W.meta[lane] = (uint32_t)sp.j_lo | ((uint32_t)sp.n_r << 10) | (sn << 26);
+                        W.r0[lane] = (uint32_t)imod(sp.u_lo, (int)S.n_rays);
+                        W.inv_nr[lane] = __frcp_ru((float)sp.n_r);
+                        ncand = nc;
+                        c.inl += nc;
+                    }
                 }
             }
         }
+        // warp prefix sum of the inline candidate counts
+        uint32_t incl = ncand;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)lane >= o) incl += t;
+        }
+        W.incl[lane] = incl;
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+        for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+            const uint32_t cc = c0 + lane;
+            if (cc < total) {
+                // owner: first lane whose inclusive prefix exceeds cc
+                uint32_t lo = 0, hi = 31;
+                while (lo < hi) {
+                    uint32_t mid = (lo + hi) >> 1;
+                    if (W.incl[mid] > cc)
+                        hi = mid;
+                    else
+                        lo = mid + 1;
+                }
+                const uint32_t own = lo;
+                const uint32_t meta = W.meta[own];
+                const uint32_t nr = (meta >> 10) & 0xFFFFu;
+                const uint32_t sn = meta >> 26;
+                uint32_t idx = cc - (own ? W.incl[own - 1] : 0u);
+                // quotient from the rounded-up reciprocal, then one correction
+                // step in each direction (idx < 2^24, so (float)idx is exact)
+                uint32_t jo = (uint32_t)((float)idx * W.inv_nr[own]);
+                if (jo * nr > idx) --jo;
+                uint32_t io = idx - jo * nr;
+                if (io >= nr) {
+                    ++jo;
+                    io -= nr;
+                }
+                const SensorDev& S = M.sens[sn];
+                const uint32_t j = (meta & 1023u) + jo;
+                uint32_t i = W.r0[own] + io;
+                if (i >= S.n_rays) i -= S.n_rays;
+                const uint32_t g = S.ray_off + j * S.n_rays + i;
+                const uint32_t tri = W.tri[own];
+                V3 d = ray_dir(M.ch[S.ch_loc + j], __ldg(&a.az_sc[S.az_off + i]));
+                float t, terr;
+                int res = test_fp32<RECHECK>(W.st[own], S, d, t, terr);
+                c.tests++;
+                if (dump) dump_candidate(a, g, tri);
+                c.hits += commit<RECHECK>(a, g, tri, res, t, terr, c.unc, c.ties);
+            }
+        }
+        __syncwarp();
     }
-    // statistics (all threads reach here)
-    warp_add(&a.counters[C_PAIRS_LIVE], c_live);
-    warp_add(&a.counters[C_CAND], c_cand);
-    warp_add(&a.counters[C_CAND_INLINE], c_inl);
-    warp_add(&a.counters[C_BIG], c_big);
-    warp_add(&a.counters[C_TESTS], c_tests);
-    warp_add(&a.counters[C_HITS], c_hits);
-    warp_add(&a.counters[C_UNCERTAIN], c_unc);
-    warp_add(&a.counters[C_TIES], c_ties);
+    c.flush(a);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_SURV] = *(volatile uint32_t*)&a.qcount[Q_SURV];
 }
 
 // ---------------------------------------------------------------------------
@@ -993,28 +1474,49 @@ __global__ void k_decode(CastArgs a, int recheck) {
 // host launchers
 // ---------------------------------------------------------------------------
 size_t cull_smem_bytes(const CastArgs& a, const LaunchCfg& cfg) {
-    size_t off = sizeof(SensorDev) * a.n_sensors + sizeof(float2) * a.total_ch;
+    size_t off = sizeof(SensorDev) * a.n_sensors + sizeof(float2) * a.total_ch + sizeof(uint16_t) * LUT_BINS * a.n_sensors;
     off = (off + 15) & ~size_t(15);
-    return off + sizeof(float) * (32 * 9 + 4) * (size_t)(cfg.cull_block / 32);
+    return off + sizeof(CullWarpSmem) * (size_t)(cfg.cull_block / 32);
 }
+static size_t cull_a_smem_bytes(const CastArgs& a, const LaunchCfg& cfg) {
+    size_t off = sizeof(SensorDev) * a.n_sensors + sizeof(float2) * a.total_ch + sizeof(uint16_t) * LUT_BINS * a.n_sensors;
+    off = (off + 15) & ~size_t(15);
+    return off + sizeof(CullAWarpSmem) * (size_t)(cfg.cull_block / 32);
+}
+static size_t cull_b_smem_bytes(const CastArgs& a) {
+    size_t off = sizeof(SensorDev) * a.n_sensors + sizeof(float2) * a.total_ch;
+    return ((off + 15) & ~size_t(15)) + sizeof(CullBWarpSmem) * 8;
+}
+
+template <typename K>
+static void ensure_smem_attr(K kernel, size_t smem) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+const char* const kKernelNames[K_NUM] = {"k_init",  "k_cull_a",       "k_cull_b",        "k_expand",
+                                          "k_test",  "k_recheck_rays", "k_recheck_pairs", "k_decode"};
 
 template <bool R, bool B>
-static void set_cull_attr(size_t smem) {
-    static size_t done = 0;
-    if (smem > 48 * 1024 && smem > done) {
-        cudaFuncSetAttribute(k_cull<R, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        done = smem;
-    }
+static void launch_cull_split(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t st,
+                              const std::function<void(int, int)>& mark) {
+    size_t sa = cull_a_smem_bytes(a, cfg), sb = cull_b_smem_bytes(a);
+    ensure_smem_attr(k_cull_a<R, B>, sa);
+    ensure_smem_attr(k_cull_b<R, B>, sb);
+    uint32_t max_blocks = (a.n_tris + cfg.cull_block - 1) / cfg.cull_block;
+    int grid_a = (int)std::min<uint32_t>(std::max<uint32_t>(max_blocks, 1u), (uint32_t)(n_sm * cfg.cull_blocks_per_sm));
+    mark(K_CULL_A, 0);
+    k_cull_a<R, B><<<grid_a, cfg.cull_block, sa, st>>>(a);
+    mark(K_CULL_A, 1);
+    mark(K_CULL_B, 0);
+    k_cull_b<R, B><<<n_sm * cfg.cull_blocks_per_sm * 2, 256, sb, st>>>(a);
+    mark(K_CULL_B, 1);
 }
-
-const char* const kKernelNames[K_NUM] = {"k_init", "k_cull", "k_expand", "k_test",
-                                          "k_recheck_rays", "k_recheck_pairs", "k_decode"};
 
 int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t st, const KernelMarks* marks) {
     const bool recheck = a.flags & 1u;
     const bool brute = a.flags & 4u;
     int launches = 0;
-    auto mark = [&](int k, int phase) {
+    std::function<void(int, int)> mark = [&](int k, int phase) {
         if (marks && marks->fn) marks->fn(marks->user, k, phase, st);
     };
     int init_blocks = (int)std::min<uint32_t>((a.n_rays_total + 255) / 256, (uint32_t)n_sm * 8);
@@ -1022,26 +1524,15 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
     k_init<<<max(init_blocks, 1), 256, 0, st>>>(a);
     mark(K_INIT, 1);
     launches++;
-    size_t smem = cull_smem_bytes(a, cfg);
-    uint32_t max_blocks = (a.n_tris + cfg.cull_block - 1) / cfg.cull_block;
-    int cull_grid = (int)std::min<uint32_t>(max_blocks, (uint32_t)(n_sm * cfg.cull_blocks_per_sm));
-    if (cull_grid < 1) cull_grid = 1;
-    mark(K_CULL, 0);
-    if (recheck && brute) {
-        set_cull_attr<true, true>(smem);
-        k_cull<true, true><<<cull_grid, cfg.cull_block, smem, st>>>(a);
-    } else if (recheck) {
-        set_cull_attr<true, false>(smem);
-        k_cull<true, false><<<cull_grid, cfg.cull_block, smem, st>>>(a);
-    } else if (brute) {
-        set_cull_attr<false, true>(smem);
-        k_cull<false, true><<<cull_grid, cfg.cull_block, smem, st>>>(a);
-    } else {
-        set_cull_attr<false, false>(smem);
-        k_cull<false, false><<<cull_grid, cfg.cull_block, smem, st>>>(a);
-    }
-    mark(K_CULL, 1);
-    launches++;
+    if (recheck && brute)
+        launch_cull_split<true, true>(a, cfg, n_sm, st, mark);
+    else if (recheck)
+        launch_cull_split<true, false>(a, cfg, n_sm, st, mark);
+    else if (brute)
+        launch_cull_split<false, true>(a, cfg, n_sm, st, mark);
+    else
+        launch_cull_split<false, false>(a, cfg, n_sm, st, mark);
+    launches += 2;
     if (!brute) {
         mark(K_EXPAND, 0);
         k_expand<<<n_sm * 8, 256, 0, st>>>(a);
@@ -1096,7 +1587,8 @@ struct NoallocLayout {
     static constexpr size_t keys = 0;                                              // u64 x max rays
     static constexpr size_t az = keys + sizeof(unsigned long long) * NOALLOC_MAX_RAYS;  // float2 x max azimuth
     static constexpr size_t ch = az + sizeof(float2) * NOALLOC_MAX_AZIMUTH;             // float2 x max channels
-    static constexpr size_t sensor = ch + sizeof(float2) * NOALLOC_MAX_CHANNELS;        // one SensorDev
+    static constexpr size_t lut = ch + sizeof(float2) * NOALLOC_MAX_CHANNELS;           // u16 x LUT_BINS
+    static constexpr size_t sensor = (lut + sizeof(uint16_t) * LUT_BINS + 15) & ~size_t(15);  // one SensorDev
     static constexpr size_t counters = (sensor + sizeof(SensorDev) + 255) & ~size_t(255);  // u64 x C_NUM
     static constexpr size_t qcount = counters + sizeof(unsigned long long) * C_NUM;        // u32 x Q_NUM
     static constexpr size_t error = qcount + sizeof(uint32_t) * Q_NUM;                     // u32
@@ -1110,6 +1602,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NoallocLayout::
 struct NoallocParams {
     SensorDev s;
     float2 ch[NOALLOC_MAX_CHANNELS];
+    uint16_t lut[LUT_BINS];
     double theta0, dtheta;
 };
 
@@ -1128,6 +1621,8 @@ __global__ void k_noalloc_prepare(NoallocParams P, unsigned char* scratch) {
         az[i] = make_float2((float)sn, (float)cs);
     }
     for (uint32_t j = tid; j < P.s.n_ch; j += stride) ch[j] = P.ch[j];
+    uint16_t* lut = reinterpret_cast<uint16_t*>(scratch + NoallocLayout::lut);
+    for (uint32_t b = tid; b < (uint32_t)LUT_BINS; b += stride) lut[b] = P.lut[b];
     if (tid == 0) *reinterpret_cast<SensorDev*>(scratch + NoallocLayout::sensor) = P.s;
     if (tid < C_NUM) reinterpret_cast<unsigned long long*>(scratch + NoallocLayout::counters)[tid] = 0ull;
     if (tid < Q_NUM) reinterpret_cast<uint32_t*>(scratch + NoallocLayout::qcount)[tid] = 0u;
@@ -1210,10 +1705,14 @@ extern "C" grca_status grca_cast_noalloc(const grca_sensor_desc* d, const float*
     double det = d->f[0] * (d->r[1] * d->u[2] - d->r[2] * d->u[1]) - d->f[1] * (d->r[0] * d->u[2] - d->r[2] * d->u[0]) +
                  d->f[2] * (d->r[0] * d->u[1] - d->r[1] * d->u[0]);
     s.hand = det < 0.0 ? -1.f : 1.f;
+    float sins[NOALLOC_MAX_CHANNELS];
     for (uint32_t j = 0; j < d->n_channels; ++j) {
         double e = d->elev_rad[j];
         P.ch[j] = make_float2((float)std::sin(e), (float)std::cos(e));
+        sins[j] = P.ch[j].x;
     }
+    build_channel_lut(sins, d->n_channels, s.lut_lo, s.lut_inv_w, P.lut);
+    s.lut_off = 0;
     P.theta0 = d->theta0;
     P.dtheta = d->dtheta;
 
@@ -1225,6 +1724,7 @@ extern "C" grca_status grca_cast_noalloc(const grca_sensor_desc* d, const float*
     a.sensors = reinterpret_cast<const SensorDev*>(scratch + NoallocLayout::sensor);
     a.ch_sc = reinterpret_cast<const float2*>(scratch + NoallocLayout::ch);
     a.az_sc = reinterpret_cast<const float2*>(scratch + NoallocLayout::az);
+    a.lut = reinterpret_cast<const uint16_t*>(scratch + NoallocLayout::lut);
     a.total_ch = d->n_channels;
     a.n_rays_total = d->n_channels * d->n_rays;
     a.keys = reinterpret_cast<unsigned long long*>(scratch + NoallocLayout::keys);

@@ -29,7 +29,7 @@ class grca_options(ctypes.Structure):
     _fields_ = [("big_pair_capacity", ctypes.c_uint64), ("chunk_capacity", ctypes.c_uint64),
                 ("recheck_capacity", ctypes.c_uint64), ("inline_max", ctypes.c_uint32),
                 ("chunk_rays", ctypes.c_uint32), ("cull_block", ctypes.c_uint32),
-                ("cull_blocks_per_sm", ctypes.c_uint32)]
+                ("cull_blocks_per_sm", ctypes.c_uint32), ("survivor_capacity", ctypes.c_uint64)]
 
 
 class grca_sensor_desc(ctypes.Structure):
@@ -40,7 +40,8 @@ class grca_sensor_desc(ctypes.Structure):
 
 
 class grca_stats(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_uint64) for n in ("pairs", "pairs_live", "candidates", "candidates_inline", "big_pairs",
+    _fields_ = [(n, ctypes.c_uint64) for n in ("pairs", "pairs_live", "survivors", "candidates", "candidates_inline",
+                                               "big_pairs",
                                                "chunks", "tests", "hits", "uncertain", "ties", "flagged_rays",
                                                "recheck_pairs", "n_rays")] + \
                [("device_error", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
