@@ -77,7 +77,7 @@ enum {
 typedef struct {
     uint64_t big_pair_capacity;  /* pairs deferred to the per-channel span pass (default 4M, 112 B each) */
     uint64_t chunk_capacity;     /* test chunks in the work queue (default 32M, 16 B each) */
-    uint64_t recheck_capacity;   /* (ray, triangle) pairs queued for FP64 re-test (default 8M, 8 B each) */
+    uint64_t recheck_capacity;   /* (ray, triangle) pairs queued for FP64 re-test (default 8M, 16 B each) */
     uint32_t inline_max;         /* candidates per pair tested inline by the culling pass (default 16) */
     uint32_t chunk_rays;         /* rays per test chunk (default 64) */
     uint32_t cull_block;         /* threads per culling block (default 256) */
@@ -126,7 +126,7 @@ typedef struct {
     uint64_t uncertain;       /* FP32 tests sent to the FP64 re-test */
     uint64_t ties;            /* tie events between FP32 hits on one ray */
     uint64_t flagged_rays;    /* rays resolved by the FP64 re-test */
-    uint64_t recheck_pairs;   /* (ray, triangle) pairs re-tested in FP64 */
+    uint64_t recheck_pairs;   /* queued (ray, triangle) pairs kept by the filter and re-tested in FP64 */
     uint64_t n_rays;          /* rays in the last cast */
     uint32_t device_error;    /* bit mask of device-side errors (0 = none) */
     uint32_t reserved;
@@ -231,7 +231,7 @@ grca_status grca_profile_enable(grca_ctx* ctx, int enable);
 
 /* Totals since grca_profile_enable: for kernel k < min(max, *n_out) of the
  * frame sequence (k_init, k_cull_a, k_cull_b, k_expand, k_test,
- * k_recheck_rays, k_recheck_pairs, k_decode), its name (static string), number of launches and
+ * k_recheck_filter, k_recheck_rays, k_recheck_pairs, k_decode), its name (static string), number of launches and
  * summed device time in ms.  Synchronizes with the recorded events.
  * *n_out receives the number of kernel kinds. */
 grca_status grca_profile_read(grca_ctx* ctx, uint32_t max, const char** names, uint64_t* launches,

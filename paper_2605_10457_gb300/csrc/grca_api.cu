@@ -93,7 +93,7 @@ struct grca_ctx {
     BigPair* d_big = nullptr;
     PairSetup* d_setups = nullptr;
     uint4* d_chunks = nullptr;
-    uint2* d_recheck = nullptr;
+    uint4* d_recheck = nullptr;
     uint32_t* d_qcount = nullptr;
     unsigned long long* d_counters = nullptr;
     uint32_t* d_error = nullptr;
@@ -261,7 +261,7 @@ grca_status grca_create(grca_ctx** out, int device, const grca_options* opt) {
         fail(e, "cudaMalloc(setups)");
     if (st == GRCA_OK && (e = cudaMalloc(&ctx->d_chunks, sizeof(uint4) * o.chunk_capacity)) != cudaSuccess)
         fail(e, "cudaMalloc(chunks)");
-    if (st == GRCA_OK && (e = cudaMalloc(&ctx->d_recheck, sizeof(uint2) * o.recheck_capacity)) != cudaSuccess)
+    if (st == GRCA_OK && (e = cudaMalloc(&ctx->d_recheck, sizeof(uint4) * o.recheck_capacity)) != cudaSuccess)
         fail(e, "cudaMalloc(recheck)");
     if (st == GRCA_OK && (e = cudaMalloc(&ctx->d_qcount, sizeof(uint32_t) * Q_NUM)) != cudaSuccess)
         fail(e, "cudaMalloc(qcount)");

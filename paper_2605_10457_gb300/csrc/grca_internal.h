@@ -126,7 +126,7 @@ struct CastArgs {
     uint4* chunks;
     uint32_t chunk_cap;
     uint32_t recheck_cap;
-    uint2* recheck;
+    uint4* recheck;           // (ray, triangle, bits of a lower bound of t, unused)
     uint32_t* qcount;
     unsigned long long* counters;
     uint32_t* error;
@@ -151,7 +151,9 @@ struct LaunchCfg {
 };
 
 // kernels of one frame, in launch order
-enum { K_INIT = 0, K_CULL_A, K_CULL_B, K_EXPAND, K_TEST, K_RECHECK_RAYS, K_RECHECK_PAIRS, K_DECODE, K_NUM };
+enum {
+    K_INIT = 0, K_CULL_A, K_CULL_B, K_EXPAND, K_TEST, K_RECHECK_FILTER, K_RECHECK_RAYS, K_RECHECK_PAIRS, K_DECODE, K_NUM
+};
 extern const char* const kKernelNames[K_NUM];
 
 // optional per-kernel hook: called with phase 0 before and phase 1 after each

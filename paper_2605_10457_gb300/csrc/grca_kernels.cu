@@ -226,10 +226,12 @@ __device__ __forceinline__ void flag_ray(const CastArgs& a, uint32_t g) {
     }
 }
 
-__device__ __forceinline__ void push_recheck(const CastArgs& a, uint32_t g, uint32_t tri) {
+// queue (ray, triangle, lower bound of t) for the FP64 re-test; the filter
+// pass keeps it only if it can still beat or tie the ray's final FP32 winner
+__device__ __forceinline__ void push_recheck(const CastArgs& a, uint32_t g, uint32_t tri, float t_lo) {
     uint32_t idx = atomicAdd(&a.qcount[Q_RECHECK], 1u);
     if (idx < a.recheck_cap)
-        a.recheck[idx] = make_uint2(g, tri);
+        a.recheck[idx] = make_uint4(g, tri, __float_as_uint(t_lo), 0u);
     else
         atomicOr(a.error, (uint32_t)ERR_RECHECK_CAP);
 }
@@ -244,7 +246,11 @@ __device__ __noinline__ void dump_candidate(const CastArgs& a, uint32_t g, uint3
     }
 }
 
-// returns 1 if a hit was committed (for the statistics)
+// Closest-hit commit.  Certain FP32 hits go into the u64 key with
+// atomicMin (after a plain L2 load that skips hits that cannot win); in the
+// recheck mode two certain hits on one ray within the tie band queue both
+// triangles, and uncertain tests queue theirs, for the FP64 re-test.
+// Returns 1 if a hit was committed (for the statistics).
 template <bool RECHECK>
 __device__ __forceinline__ int commit(const CastArgs& a, uint32_t g, uint32_t tri, int res, float t, float t_err,
                                       uint32_t& n_unc, uint32_t& n_ties) {
@@ -254,9 +260,9 @@ __device__ __forceinline__ int commit(const CastArgs& a, uint32_t g, uint32_t tr
     float tcur = __uint_as_float((uint32_t)(cur >> 32));
     if (res == T_UNCERTAIN) {
         // a re-test can only change the result if it may beat the current best
-        if (t_err < 0.25f && t > 0.f && t * (1.f - t_err) > tcur * (1.f + BETA)) return 0;
-        flag_ray(a, g);
-        push_recheck(a, g, tri);
+        bool t_ok = t_err < 0.25f && t > 0.f;
+        if (t_ok && t * (1.f - t_err) > tcur * (1.f + BETA)) return 0;
+        push_recheck(a, g, tri, t_ok ? t * (1.f - t_err) : 0.f);
         n_unc++;
         return 0;
     }
@@ -271,9 +277,8 @@ __device__ __forceinline__ int commit(const CastArgs& a, uint32_t g, uint32_t tr
     if (oid != NO_HIT && oid != tri) {
         float told = __uint_as_float((uint32_t)(old >> 32));
         if (fabsf(t - told) <= BETA * fmaxf(t, told)) {
-            flag_ray(a, g);
-            push_recheck(a, g, tri);
-            push_recheck(a, g, oid);
+            push_recheck(a, g, tri, t * (1.f - TAU_T));
+            push_recheck(a, g, oid, told * (1.f - TAU_T));
             n_ties++;
         }
     }
@@ -980,13 +985,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
 // ---------------------------------------------------------------------------
 struct CullBWarpSmem {
     PairSetup st[32];
-    uint32_t incl[32];    // inclusive prefix of candidate counts
-    uint32_t tri[32];
-    uint32_t meta[32];    // j_lo | n_r << 10 | sensor << 26
-    uint32_t r0[32];
-    float inv_nr[32];     // 1 / n_r (rounded up), for the candidate -> (channel, ray) split
 };
-
 template <bool RECHECK, bool BRUTE>
 __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1000,7 +999,8 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
     const uint32_t gwarp = ((blockIdx.x * blockDim.x) >> 5) + wib;
     for (uint32_t b0 = gwarp * 32; b0 < n; b0 += n_warps * 32) {
         const uint32_t q = b0 + lane;
-        uint32_t ncand = 0;
+        uint32_t ncand = 0, my_tri = 0, my_meta = 0, my_r0 = 0;
+        float my_inv = 0.f;
         if (q < n) {
             const unsigned long long r = __ldcs(&a.surv[q]);
             const uint32_t tri = (uint32_t)r, span = (uint32_t)(r >> 32) & 0x1FFFFFu, sn = (uint32_t)(r >> 53);
@@ -1088,10 +1088,10 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
                     bool det_unc = fabsf(det) <= err_det;
                     if (det != 0.f || (RECHECK && det_unc)) {
                         make_setup(S, T, w, p, det, err_det, W.st[lane]);
-                        W.tri[lane] = tri;
-                        W.meta[lane] = (uint32_t)sp.j_lo | ((uint32_t)sp.n_r << 10) | (sn << 26);
-                        W.r0[lane] = (uint32_t)imod(sp.u_lo, (int)S.n_rays);
-                        W.inv_nr[lane] = __frcp_ru((float)sp.n_r);
+                        my_tri = tri;
+                        my_meta = (uint32_t)sp.j_lo | ((uint32_t)sp.n_r << 10) | (sn << 26);
+                        my_r0 = (uint32_t)imod(sp.u_lo, (int)S.n_rays);
+                        my_inv = __frcp_ru((float)sp.n_r);
                         ncand = nc;
                         c.inl += nc;
                     }
@@ -1105,29 +1105,31 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
             uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
             if ((int)lane >= o) incl += t;
         }
-        W.incl[lane] = incl;
+        const uint32_t excl = incl - ncand;
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t nz = __ballot_sync(0xffffffffu, ncand > 0);   // lanes that own candidates, in order
         __syncwarp();
         for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+            // rank (among owning lanes) of the pair holding candidate c0, and the
+            // pairs that start inside this round of 32 candidates
+            const uint32_t base_rank = __popc(__ballot_sync(0xffffffffu, ncand > 0 && incl <= c0));
+            const uint32_t starts =
+                __reduce_or_sync(0xffffffffu, (ncand > 0 && excl > c0 && excl < c0 + 32) ? (1u << (excl - c0)) : 0u);
+            const uint32_t rank = base_rank + __popc(starts & ((2u << lane) - 2u));
+            const uint32_t own = __fns(nz, 0, (int)min(rank, 31u) + 1);
+            const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, own & 31u);
+            const uint32_t meta = __shfl_sync(0xffffffffu, my_meta, own & 31u);
+            const uint32_t r0o = __shfl_sync(0xffffffffu, my_r0, own & 31u);
+            const uint32_t tri = __shfl_sync(0xffffffffu, my_tri, own & 31u);
+            const float inv = __shfl_sync(0xffffffffu, my_inv, own & 31u);
             const uint32_t cc = c0 + lane;
             if (cc < total) {
-                // owner: first lane whose inclusive prefix exceeds cc
-                uint32_t lo = 0, hi = 31;
-                while (lo < hi) {
-                    uint32_t mid = (lo + hi) >> 1;
-                    if (W.incl[mid] > cc)
-                        hi = mid;
-                    else
-                        lo = mid + 1;
-                }
-                const uint32_t own = lo;
-                const uint32_t meta = W.meta[own];
                 const uint32_t nr = (meta >> 10) & 0xFFFFu;
                 const uint32_t sn = meta >> 26;
-                uint32_t idx = cc - (own ? W.incl[own - 1] : 0u);
+                uint32_t idx = cc - o_excl;
                 // quotient from the rounded-up reciprocal, then one correction
                 // step in each direction (idx < 2^24, so (float)idx is exact)
-                uint32_t jo = (uint32_t)((float)idx * W.inv_nr[own]);
+                uint32_t jo = (uint32_t)((float)idx * inv);
                 if (jo * nr > idx) --jo;
                 uint32_t io = idx - jo * nr;
                 if (io >= nr) {
@@ -1136,13 +1138,12 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
                 }
                 const SensorDev& S = M.sens[sn];
                 const uint32_t j = (meta & 1023u) + jo;
-                uint32_t i = W.r0[own] + io;
+                uint32_t i = r0o + io;
                 if (i >= S.n_rays) i -= S.n_rays;
                 const uint32_t g = S.ray_off + j * S.n_rays + i;
-                const uint32_t tri = W.tri[own];
                 V3 d = ray_dir(M.ch[S.ch_loc + j], __ldg(&a.az_sc[S.az_off + i]));
                 float t, terr;
-                int res = test_fp32<RECHECK>(W.st[own], S, d, t, terr);
+                int res = test_fp32<RECHECK>(W.st[own & 31u], S, d, t, terr);
                 c.tests++;
                 if (dump) dump_candidate(a, g, tri);
                 c.hits += commit<RECHECK>(a, g, tri, res, t, terr, c.unc, c.ties);
@@ -1435,6 +1436,21 @@ __device__ unsigned long long test_fp64(const CastArgs& a, uint32_t g, uint32_t 
     return ((unsigned long long)__float_as_uint(tf) << 32) | tri;
 }
 
+// R0: keep the queued pairs that can still beat or tie the ray's final FP32
+// winner (t_lo <= t_best (1 + beta)); flag their rays; drop the rest
+__global__ void k_recheck_filter(CastArgs a) {
+    uint32_t np = min(*(volatile uint32_t*)&a.qcount[Q_RECHECK], a.recheck_cap);
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
+        uint4 e = a.recheck[q];
+        float tbest = __uint_as_float((uint32_t)(a.keys[e.x] >> 32));
+        if (__uint_as_float(e.z) <= tbest * (1.f + BETA)) {
+            flag_ray(a, e.x);
+        } else {
+            a.recheck[q].y = NO_HIT;
+        }
+    }
+}
+
 // R1: every flagged ray starts from the FP64 result of its FP32 winner
 __global__ void k_recheck_rays(CastArgs a) {
     uint32_t nf = min(*(volatile uint32_t*)&a.qcount[Q_FLAG], a.flag_cap);
@@ -1447,15 +1463,19 @@ __global__ void k_recheck_rays(CastArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_FLAGGED] = *(volatile uint32_t*)&a.qcount[Q_FLAG];
 }
 
-// R2: FP64 re-test of every queued (ray, triangle) pair
+// R2: FP64 re-test of every kept (ray, triangle) pair
 __global__ void k_recheck_pairs(CastArgs a) {
     uint32_t np = min(*(volatile uint32_t*)&a.qcount[Q_RECHECK], a.recheck_cap);
+    uint32_t kept = 0;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
-        uint2 pr = a.recheck[q];
+        uint4 pr = a.recheck[q];
+        if (pr.y == NO_HIT) continue;
+        kept++;
         unsigned long long k = test_fp64(a, pr.x, pr.y);
         if (k != KEY_MISS) atomicMin(&a.keys64[pr.x], k);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_RECHECK] = *(volatile uint32_t*)&a.qcount[Q_RECHECK];
+    kept = __reduce_add_sync(0xffffffffu, kept);
+    if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&a.counters[C_RECHECK], (unsigned long long)kept);
 }
 
 // R3 fused into decode: flagged rays take the FP64 key
@@ -1493,8 +1513,9 @@ static void ensure_smem_attr(K kernel, size_t smem) {
     if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-const char* const kKernelNames[K_NUM] = {"k_init",  "k_cull_a",       "k_cull_b",        "k_expand",
-                                          "k_test",  "k_recheck_rays", "k_recheck_pairs", "k_decode"};
+const char* const kKernelNames[K_NUM] = {"k_init",           "k_cull_a",       "k_cull_b",
+                                          "k_expand",         "k_test",         "k_recheck_filter",
+                                          "k_recheck_rays",   "k_recheck_pairs", "k_decode"};
 
 template <bool R, bool B>
 static void launch_cull_split(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t st,
@@ -1546,13 +1567,16 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
         launches += 2;
     }
     if (recheck) {
+        mark(K_RECHECK_FILTER, 0);
+        k_recheck_filter<<<n_sm * 2, 256, 0, st>>>(a);
+        mark(K_RECHECK_FILTER, 1);
         mark(K_RECHECK_RAYS, 0);
         k_recheck_rays<<<n_sm * 2, 256, 0, st>>>(a);
         mark(K_RECHECK_RAYS, 1);
         mark(K_RECHECK_PAIRS, 0);
         k_recheck_pairs<<<n_sm * 2, 256, 0, st>>>(a);
         mark(K_RECHECK_PAIRS, 1);
-        launches += 2;
+        launches += 3;
     }
     int dec_blocks = (int)std::min<uint32_t>((a.n_rays_total + 255) / 256, (uint32_t)n_sm * 8);
     mark(K_DECODE, 0);

@@ -67,16 +67,23 @@ def grade(orc: "oracle.Oracle", tris: np.ndarray, ref: dict, gpu_t: np.ndarray, 
 
 
 def stratified_rays(sensors, n_per_sensor: int, seed: int = 0) -> np.ndarray:
-    """Every channel, evenly strided rays with a seeded phase, per sensor."""
+    """About n_per_sensor rays per sensor: evenly strided channels (all of them
+    when the budget allows), evenly strided rays with a seeded phase."""
     rng = np.random.default_rng(seed)
     out = []
     off = 0
     for s in sensors:
-        per_ch = max(1, n_per_sensor // s.n_channels)
+        if n_per_sensor >= s.n_channels:
+            chans = np.arange(s.n_channels)
+        else:
+            step_c = s.n_channels / max(1, n_per_sensor)
+            chans = np.unique((np.arange(n_per_sensor) * step_c + rng.uniform(0, step_c)).astype(np.int64))
+            chans = chans[chans < s.n_channels]
+        per_ch = max(1, n_per_sensor // len(chans))
         step = max(1, s.n_rays // per_ch)
-        for j in range(s.n_channels):
+        for j in chans:
             ph = int(rng.integers(step))
             i = np.arange(ph, s.n_rays, step)[:per_ch]
-            out.append(off + j * s.n_rays + i)
+            out.append(off + int(j) * s.n_rays + i)
         off += s.n_channels * s.n_rays
     return np.unique(np.concatenate(out).astype(np.int64))
