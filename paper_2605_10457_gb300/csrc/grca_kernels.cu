@@ -252,11 +252,10 @@ __device__ __noinline__ void dump_candidate(const CastArgs& a, uint32_t g, uint3
 // triangles, and uncertain tests queue theirs, for the FP64 re-test.
 // Returns 1 if a hit was committed (for the statistics).
 template <bool RECHECK>
-__device__ __forceinline__ int commit(const CastArgs& a, uint32_t g, uint32_t tri, int res, float t, float t_err,
-                                      uint32_t& n_unc, uint32_t& n_ties) {
+__device__ __forceinline__ int commit_pre(const CastArgs& a, uint32_t g, uint32_t tri, int res, float t, float t_err,
+                                          unsigned long long cur, uint32_t& n_unc, uint32_t& n_ties) {
     if (res == T_MISS) return 0;
     unsigned long long* kp = &a.keys[g];
-    unsigned long long cur = __ldcg(kp);
     float tcur = __uint_as_float((uint32_t)(cur >> 32));
     if (res == T_UNCERTAIN) {
         // a re-test can only change the result if it may beat the current best
@@ -283,6 +282,13 @@ __device__ __forceinline__ int commit(const CastArgs& a, uint32_t g, uint32_t tr
         }
     }
     return 1;
+}
+
+template <bool RECHECK>
+__device__ __forceinline__ int commit(const CastArgs& a, uint32_t g, uint32_t tri, int res, float t, float t_err,
+                                      uint32_t& n_unc, uint32_t& n_ties) {
+    if (res == T_MISS) return 0;
+    return commit_pre<RECHECK>(a, g, tri, res, t, t_err, __ldcg(&a.keys[g]), n_unc, n_ties);
 }
 
 // ---------------------------------------------------------------------------
@@ -463,14 +469,18 @@ __device__ __forceinline__ int lut_bin(const SensorDev& S, float x) {
     float fb = (x - S.lut_lo) * S.lut_inv_w;
     return fb <= 0.f ? 0 : (fb >= (float)(LUT_BINS - 1) ? LUT_BINS - 1 : (int)fb);
 }
-__device__ __forceinline__ int chan_lower(const SensorDev& S, const float2* ch, const uint16_t* lut, float x) {
+__device__ __forceinline__ float sin_at(const float* t, int j) { return t[j]; }
+__device__ __forceinline__ float sin_at(const float2* t, int j) { return t[j].x; }
+template <typename T>
+__device__ __forceinline__ int chan_lower(const SensorDev& S, const T* ch, const uint16_t* lut, float x) {
     int j = lut[lut_bin(S, x)], n = (int)S.n_ch;
-    while (j < n && ch[j].x < x) ++j;
+    while (j < n && sin_at(ch, j) < x) ++j;
     return j;
 }
-__device__ __forceinline__ int chan_upper(const SensorDev& S, const float2* ch, const uint16_t* lut, float x) {
+template <typename T>
+__device__ __forceinline__ int chan_upper(const SensorDev& S, const T* ch, const uint16_t* lut, float x) {
     int j = lut[lut_bin(S, x)], n = (int)S.n_ch;
-    while (j < n && ch[j].x <= x) ++j;
+    while (j < n && sin_at(ch, j) <= x) ++j;
     return j;
 }
 
@@ -669,8 +679,8 @@ __device__ __forceinline__ uint32_t pack_span(int jl, int jh, bool pierced) {
 
 // Phase A of one (triangle, sensor) pair: back-face cull (if requested) and
 // the channel span from the elevation range.  Returns false when culled.
-template <bool RECHECK, bool BRUTE>
-__device__ __forceinline__ bool cull_elevation(const SensorDev& S, const float2* ch, const uint16_t* lut, const V3 v[3],
+template <bool RECHECK, bool BRUTE, typename T>
+__device__ __forceinline__ bool cull_elevation(const SensorDev& S, const T* ch, const uint16_t* lut, const V3 v[3],
                                                const V3& nw, bool cull_back, uint32_t& span) {
     V3 w0 = rel_origin(S, v[0]);
     if (cull_back) {
@@ -690,7 +700,7 @@ __device__ __forceinline__ bool cull_elevation(const SensorDev& S, const float2*
     float smin, smax;
     bool pierced = elev_range_w(S, wv, smin, smax);
     int jl = chan_lower(S, ch, lut, smin - EPS_S);
-    if (jl >= (int)S.n_ch || ch[jl].x > smax + EPS_S) return false;  // no channel in the range
+    if (jl >= (int)S.n_ch || sin_at(ch, jl) > smax + EPS_S) return false;  // no channel in the range
     int jh = chan_upper(S, ch, lut, smax + EPS_S) - 1;
     span = pack_span(jl, jh, pierced);
     return true;
@@ -711,8 +721,9 @@ __device__ __forceinline__ void cull_rest(const CastArgs& a, const SensorDev& S,
     }
     if (!BRUTE && S.has_range) {
         // range cull (App. A.4.1 Step 1), only where provably empty
-        float dmax = fmaxf(vnorm(w[0]), fmaxf(vnorm(w[1]), vnorm(w[2])));
-        if (dmax < S.d_min * (1.f - 1e-5f) - 1e-6f) return;
+        float dmax2 = fmaxf(vdot(w[0], w[0]), fmaxf(vdot(w[1], w[1]), vdot(w[2], w[2])));
+        float dlo = fmaxf(S.d_min * (1.f - 1e-5f) - 1e-6f, 0.f);
+        if (dmax2 < dlo * dlo) return;
         if (S.d_max < INFINITY && closest_dist(w[0], w[1], w[2]) > S.d_max * (1.f + 1e-5f) + 1e-6f) return;
     }
     Span sp;
@@ -916,20 +927,52 @@ __global__ void __launch_bounds__(256, 3) k_cull(CastArgs a) {
 // per-warp shared-memory buffer (one atomic per flush of >= 256 entries)
 // record: tri | span << 32 | sensor << 53
 // ---------------------------------------------------------------------------
-constexpr int SURV_BUF = 384;  // >= 32 * CULL_GROUP + some slack
+constexpr int CULL_A_GROUP = 4;  // sensors per step of k_cull_a (bounds the entries a step adds)
+constexpr int SURV_BUF = 352;    // per-warp survivor buffer; flushed before a step could overflow it
+constexpr int MAX_SENSORS_SORT = 64;
 struct CullAWarpSmem {
     float tri[32 * 9 + 4];
     unsigned long long buf[SURV_BUF];
+    uint16_t rank[SURV_BUF];            // rank of each entry within its sensor's bucket
+    uint32_t hist[MAX_SENSORS_SORT];    // per-sensor counts, then bucket offsets
 };
 static_assert(sizeof(CullAWarpSmem) % 16 == 0, "per-warp staging must stay 16-byte aligned");
+static_assert(SURV_BUF >= 32 * CULL_A_GROUP, "a step must fit an empty buffer");
 
-__device__ __forceinline__ void flush_survivors(const CastArgs& a, CullAWarpSmem& W, uint32_t& fill, uint32_t lane) {
+// Flush a warp's survivor buffer to the global queue, counting-sorted by
+// sensor so that k_cull_b's batches of 32 mostly hold one sensor (uniform
+// descriptor reads, one azimuth table per batch in L1).
+__device__ __forceinline__ void flush_survivors(const CastArgs& a, CullAWarpSmem& W, uint32_t& fill, uint32_t lane,
+                                                uint32_t n_sensors) {
+    if (fill == 0) return;
+    for (uint32_t s = lane; s < n_sensors; s += 32) W.hist[s] = 0;
+    __syncwarp();
+    for (uint32_t q = lane; q < fill; q += 32) W.rank[q] = (uint16_t)atomicAdd(&W.hist[W.buf[q] >> 53], 1u);
+    __syncwarp();
+    // exclusive prefix over the sensor counts (n_sensors <= 64: two per lane)
+    uint32_t h0 = lane < n_sensors ? W.hist[lane] : 0u, h1 = lane + 32 < n_sensors ? W.hist[lane + 32] : 0u;
+    uint32_t i0 = h0, i1 = h1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t0 = __shfl_up_sync(0xffffffffu, i0, o), t1 = __shfl_up_sync(0xffffffffu, i1, o);
+        if ((int)lane >= o) {
+            i0 += t0;
+            i1 += t1;
+        }
+    }
+    uint32_t tot0 = __shfl_sync(0xffffffffu, i0, 31);
+    __syncwarp();
+    if (lane < n_sensors) W.hist[lane] = i0 - h0;
+    if (lane + 32 < n_sensors) W.hist[lane + 32] = tot0 + i1 - h1;
     uint32_t b0 = 0;
-    if (lane == 0 && fill) b0 = atomicAdd(&a.qcount[Q_SURV], fill);
+    if (lane == 0) b0 = atomicAdd(&a.qcount[Q_SURV], fill);
     b0 = __shfl_sync(0xffffffffu, b0, 0);
+    __syncwarp();
     for (uint32_t q = lane; q < fill; q += 32) {
-        if (b0 + q < a.surv_cap)
-            a.surv[b0 + q] = W.buf[q];
+        unsigned long long e = W.buf[q];
+        uint32_t dst = b0 + W.hist[e >> 53] + W.rank[q];
+        if (dst < a.surv_cap)
+            a.surv[dst] = e;
         else
             atomicOr(a.error, (uint32_t)ERR_SURV_CAP);
     }
@@ -937,10 +980,36 @@ __device__ __forceinline__ void flush_survivors(const CastArgs& a, CullAWarpSmem
     fill = 0;
 }
 
+// prologue of k_cull_a: sensor descriptors, channel sines and lookup tables
+struct CullASmem {
+    SensorDev* sens;
+    float* sins;
+    uint16_t* lut;
+    unsigned char* rest;
+};
+__device__ __forceinline__ CullASmem cull_a_prologue(const CastArgs& a, unsigned char* smem) {
+    CullASmem m;
+    m.sens = reinterpret_cast<SensorDev*>(smem);
+    m.sins = reinterpret_cast<float*>(smem + sizeof(SensorDev) * a.n_sensors);
+    m.lut = reinterpret_cast<uint16_t*>(smem + sizeof(SensorDev) * a.n_sensors + sizeof(float) * a.total_ch);
+    size_t off = sizeof(SensorDev) * a.n_sensors + sizeof(float) * a.total_ch + sizeof(uint16_t) * LUT_BINS * a.n_sensors;
+    m.rest = smem + ((off + 15) & ~size_t(15));
+    for (uint32_t q = threadIdx.x; q < a.n_sensors * (uint32_t)(sizeof(SensorDev) / 4); q += blockDim.x)
+        reinterpret_cast<uint32_t*>(m.sens)[q] = reinterpret_cast<const uint32_t*>(a.sensors)[q];
+    __syncthreads();
+    for (uint32_t sn = 0; sn < a.n_sensors; ++sn) {
+        const SensorDev& S = m.sens[sn];
+        for (uint32_t j = threadIdx.x; j < S.n_ch; j += blockDim.x) m.sins[S.ch_loc + j] = a.ch_sc[S.ch_off + j].x;
+        for (uint32_t b = threadIdx.x; b < LUT_BINS; b += blockDim.x) m.lut[sn * LUT_BINS + b] = a.lut[S.lut_off + b];
+    }
+    __syncthreads();
+    return m;
+}
+
 template <bool RECHECK, bool BRUTE>
 __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    CullSmem M = cull_smem_prologue(a, smem, true);
+    CullASmem M = cull_a_prologue(a, smem);
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     CullAWarpSmem& W = reinterpret_cast<CullAWarpSmem*>(M.rest)[wib];
     const bool cull_back = a.flags & 2u;
@@ -955,13 +1024,14 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
         V3 v[3] = {{t9[0], t9[1], t9[2]}, {t9[3], t9[4], t9[5]}, {t9[6], t9[7], t9[8]}};
         V3 nw = vcross(vsub(v[1], v[0]), vsub(v[2], v[0]));
         if (nw.x == 0.f && nw.y == 0.f && nw.z == 0.f) valid = false;  // zero area: never hit
-        for (uint32_t sg = 0; sg < a.n_sensors; sg += CULL_GROUP) {
-            const uint32_t ng = min((uint32_t)CULL_GROUP, a.n_sensors - sg);
-            if (fill + 32 * CULL_GROUP > SURV_BUF) flush_survivors(a, W, fill, lane);
+        for (uint32_t sg = 0; sg < a.n_sensors; sg += CULL_A_GROUP) {
+            const uint32_t ng = min((uint32_t)CULL_A_GROUP, a.n_sensors - sg);
+            if (fill + 32 * CULL_A_GROUP > SURV_BUF) flush_survivors(a, W, fill, lane, a.n_sensors);
             for (uint32_t k = 0; k < ng; ++k) {
                 uint32_t span = 0;
-                bool ok = valid && cull_elevation<RECHECK, BRUTE>(M.sens[sg + k], M.ch + M.sens[sg + k].ch_loc,
-                                                                  M.lut + (sg + k) * LUT_BINS, v, nw, cull_back, span);
+                const SensorDev& S = M.sens[sg + k];
+                bool ok = valid && cull_elevation<RECHECK, BRUTE>(S, M.sins + S.ch_loc, M.lut + (sg + k) * LUT_BINS, v,
+                                                                  nw, cull_back, span);
                 uint32_t bal = __ballot_sync(0xffffffffu, ok);
                 if (ok)
                     W.buf[fill + __popc(bal & ((1u << lane) - 1u))] =
@@ -972,7 +1042,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
             __syncwarp();
         }
     }
-    flush_survivors(a, W, fill, lane);
+    flush_survivors(a, W, fill, lane, a.n_sensors);
 }
 
 // ---------------------------------------------------------------------------
@@ -1019,8 +1089,9 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
             bool keep = true;
             if (!BRUTE && S.has_range) {
                 // range cull (App. A.4.1 Step 1), only where provably empty
-                float dmax = fmaxf(vnorm(w[0]), fmaxf(vnorm(w[1]), vnorm(w[2])));
-                if (dmax < S.d_min * (1.f - 1e-5f) - 1e-6f) keep = false;
+                float dmax2 = fmaxf(vdot(w[0], w[0]), fmaxf(vdot(w[1], w[1]), vdot(w[2], w[2])));
+                float dlo = fmaxf(S.d_min * (1.f - 1e-5f) - 1e-6f, 0.f);
+                if (dmax2 < dlo * dlo) keep = false;
                 if (keep && S.d_max < INFINITY && closest_dist(w[0], w[1], w[2]) > S.d_max * (1.f + 1e-5f) + 1e-6f)
                     keep = false;
             }
@@ -1141,12 +1212,13 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
                 uint32_t i = r0o + io;
                 if (i >= S.n_rays) i -= S.n_rays;
                 const uint32_t g = S.ray_off + j * S.n_rays + i;
+                const unsigned long long cur = __ldcg(&a.keys[g]);   // issued before the test arithmetic
                 V3 d = ray_dir(M.ch[S.ch_loc + j], __ldg(&a.az_sc[S.az_off + i]));
                 float t, terr;
                 int res = test_fp32<RECHECK>(W.st[own & 31u], S, d, t, terr);
                 c.tests++;
                 if (dump) dump_candidate(a, g, tri);
-                c.hits += commit<RECHECK>(a, g, tri, res, t, terr, c.unc, c.ties);
+                c.hits += commit_pre<RECHECK>(a, g, tri, res, t, terr, cur, c.unc, c.ties);
             }
         }
         __syncwarp();
@@ -1499,7 +1571,7 @@ size_t cull_smem_bytes(const CastArgs& a, const LaunchCfg& cfg) {
     return off + sizeof(CullWarpSmem) * (size_t)(cfg.cull_block / 32);
 }
 static size_t cull_a_smem_bytes(const CastArgs& a, const LaunchCfg& cfg) {
-    size_t off = sizeof(SensorDev) * a.n_sensors + sizeof(float2) * a.total_ch + sizeof(uint16_t) * LUT_BINS * a.n_sensors;
+    size_t off = sizeof(SensorDev) * a.n_sensors + sizeof(float) * a.total_ch + sizeof(uint16_t) * LUT_BINS * a.n_sensors;
     off = (off + 15) & ~size_t(15);
     return off + sizeof(CullAWarpSmem) * (size_t)(cfg.cull_block / 32);
 }
