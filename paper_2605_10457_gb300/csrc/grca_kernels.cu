@@ -27,6 +27,7 @@
 // ray passes between them.  t = ((v0-o).n) / (d.n).
 #include <cooperative_groups.h>
 #include <algorithm>
+#include <cstddef>
 #include <functional>
 #include <cmath>
 #include <cstring>
@@ -118,8 +119,22 @@ __device__ __forceinline__ V3 rel_origin(const SensorDev& S, V3 v) {
 // ---------------------------------------------------------------------------
 // test setup of one (triangle, sensor) pair
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void make_setup(const SensorDev& S, const TriW& T, const V3 w[3], const V3 p[3],
-                                           float det, float err_det_abs, PairSetup& st) {
+// Setup outputs go through a writer: set(k, value) with the field index of
+// the setup views below (m 0-8, tau 9-11, n 12-14, det 15, err_det 16,
+// state 17, G 18-20).
+struct SetupWriterAoS {
+    PairSetup& s;
+    __device__ __forceinline__ void set(int k, float v) { reinterpret_cast<float*>(&s)[k] = v; }
+};
+struct SetupWriterSoA {
+    float* base;  // [21][32]
+    uint32_t i;
+    __device__ __forceinline__ void set(int k, float v) { base[k * 32 + i] = v; }
+};
+
+template <typename WR>
+__device__ __forceinline__ void make_setup(const SensorDev& S, const TriW& T, const V3 w[3], const V3 p[3], float det,
+                                           float err_det_abs, WR out) {
     bool unc = fabsf(det) <= err_det_abs;
     // forward hit <=> every emitter-frame edge function has the sign of the
     // emitter-frame triple product p0.(p1 x p2) = det(B) * det
@@ -130,29 +145,32 @@ __device__ __forceinline__ void make_setup(const SensorDev& S, const TriW& T, co
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         V3 e = rotB(S.B, T.E[k]);
-        V3 m = vcross(p[T.base[k]], e);
+        // base vertex by selects (a runtime index would put p[] in local memory)
+        const int b = T.base[k];
+        const V3 pb = b == 0 ? p[0] : (b == 1 ? p[1] : p[2]);
+        const float rb = b == 0 ? r2[0] : (b == 1 ? r2[1] : r2[2]);
+        V3 m = vcross(pb, e);
         float f = T.sg[k] * fold;
         if (f < 0.f) m = vneg(m);
-        st.m[3 * k + 0] = m.x;
-        st.m[3 * k + 1] = m.y;
-        st.m[3 * k + 2] = m.z;
+        out.set(3 * k + 0, m.x);
+        out.set(3 * k + 1, m.y);
+        out.set(3 * k + 2, m.z);
         // FP32 error bound of d.m: errors of p_base, e (rotation, origin) and of
         // the cross and dot products, all <= 18 u |p_base| |e| (|m| <= |p_base| |e|)
         float ee = T.E[k].x * T.E[k].x + T.E[k].y * T.E[k].y + T.E[k].z * T.E[k].z;
-        st.tau[k] = 18.f * U32 * sqrtf(r2[T.base[k]] * ee) + 1e-30f;
+        out.set(9 + k, 18.f * U32 * sqrtf(rb * ee) + 1e-30f);
     }
     V3 ne = rotB(S.B, T.n);
-    st.n[0] = ne.x;
-    st.n[1] = ne.y;
-    st.n[2] = ne.z;
-    st.det = det;
-    st.err_det = det != 0.f ? err_det_abs / fabsf(det) : 1.f;
-    st.state = unc ? 1u : 0u;
+    out.set(12, ne.x);
+    out.set(13, ne.y);
+    out.set(14, ne.z);
+    out.set(15, det);
+    out.set(16, det != 0.f ? err_det_abs / fabsf(det) : 1.f);
+    out.set(17, __uint_as_float(unc ? 1u : 0u));
     float q0 = 3.f * (fabsf(T.n.x) + T.N.x), q1 = 3.f * (fabsf(T.n.y) + T.N.y), q2 = 3.f * (fabsf(T.n.z) + T.N.z);
-    st.G[0] = U32 * (fabsf(S.B[0]) * q0 + fabsf(S.B[1]) * q1 + fabsf(S.B[2]) * q2 + 6.f * fabsf(ne.x));
-    st.G[1] = U32 * (fabsf(S.B[3]) * q0 + fabsf(S.B[4]) * q1 + fabsf(S.B[5]) * q2 + 6.f * fabsf(ne.y));
-    st.G[2] = U32 * (fabsf(S.B[6]) * q0 + fabsf(S.B[7]) * q1 + fabsf(S.B[8]) * q2 + 6.f * fabsf(ne.z));
-    st.pad_ = 0.f;
+    out.set(18, U32 * (fabsf(S.B[0]) * q0 + fabsf(S.B[1]) * q1 + fabsf(S.B[2]) * q2 + 6.f * fabsf(ne.x)));
+    out.set(19, U32 * (fabsf(S.B[3]) * q0 + fabsf(S.B[4]) * q1 + fabsf(S.B[5]) * q2 + 6.f * fabsf(ne.y)));
+    out.set(20, U32 * (fabsf(S.B[6]) * q0 + fabsf(S.B[7]) * q1 + fabsf(S.B[8]) * q2 + 6.f * fabsf(ne.z)));
 }
 
 __device__ __forceinline__ float det_error(const V3& w0, const TriW& T) {
@@ -173,31 +191,50 @@ __device__ __forceinline__ V3 ray_dir(float2 ch, float2 az) {
 // FP32 test.  Plain mode: inclusive edge test, T_HIT or T_MISS.  Recheck mode
 // additionally returns T_UNCERTAIN when the FP32 decision or t is not
 // guaranteed; *t_err receives the relative error bound of t.
-template <bool RECHECK>
-__device__ __forceinline__ int test_fp32(const PairSetup& st, const SensorDev& S, V3 d, float& t, float& t_err) {
-    V3 m0 = {st.m[0], st.m[1], st.m[2]}, m1 = {st.m[3], st.m[4], st.m[5]}, m2 = {st.m[6], st.m[7], st.m[8]};
+// A pair setup is read through a view: the PairSetup struct itself, or one
+// lane's column of a field-major shared-memory copy (conflict-free).
+// Field index: m 0-8, tau 9-11, n 12-14, det 15, err_det 16, state 17, G 18-20.
+constexpr int SETUP_FIELDS = 21;
+static_assert(offsetof(PairSetup, tau) == 9 * 4 && offsetof(PairSetup, n) == 12 * 4 && offsetof(PairSetup, det) == 15 * 4 &&
+                  offsetof(PairSetup, err_det) == 16 * 4 && offsetof(PairSetup, state) == 17 * 4 &&
+                  offsetof(PairSetup, G) == 18 * 4,
+              "setup field indices");
+struct SetupAoS {
+    const PairSetup& s;
+    __device__ __forceinline__ float f(int k) const { return reinterpret_cast<const float*>(&s)[k]; }
+};
+struct SetupSoA {
+    const float* base;  // [SETUP_FIELDS][32]
+    uint32_t i;
+    __device__ __forceinline__ float f(int k) const { return base[k * 32 + i]; }
+};
+
+template <bool RECHECK, typename SV>
+__device__ __forceinline__ int test_fp32(const SV& st, const SensorDev& S, V3 d, float& t, float& t_err) {
+    V3 m0 = {st.f(0), st.f(1), st.f(2)}, m1 = {st.f(3), st.f(4), st.f(5)}, m2 = {st.f(6), st.f(7), st.f(8)};
     float E0 = vdot(d, m0), E1 = vdot(d, m1), E2 = vdot(d, m2);
-    float dn = vdot(d, {st.n[0], st.n[1], st.n[2]});
-    t = __fdiv_rn(st.det, dn);
+    float dn = vdot(d, {st.f(12), st.f(13), st.f(14)});
+    t = __fdiv_rn(st.f(15), dn);
     t_err = 0.f;
     if (!RECHECK) {
         if (E0 < 0.f || E1 < 0.f || E2 < 0.f) return T_MISS;
         if (!(t > 0.f) || !(t <= S.d_max) || t < S.d_min) return T_MISS;
         return T_HIT;
     }
-    bool unc_pair = st.state & 1u;
-    if (E0 < -st.tau[0] || E1 < -st.tau[1] || E2 < -st.tau[2]) {
+    const float tau0 = st.f(9), tau1 = st.f(10), tau2 = st.f(11);
+    bool unc_pair = __float_as_uint(st.f(17)) & 1u;
+    if (E0 < -tau0 || E1 < -tau1 || E2 < -tau2) {
         if (!unc_pair) return T_MISS;
         // orientation unknown: the other orientation may still hold
-        if (E0 <= st.tau[0] && E1 <= st.tau[1] && E2 <= st.tau[2]) {
+        if (E0 <= tau0 && E1 <= tau1 && E2 <= tau2) {
             t_err = 1.f;
             return T_UNCERTAIN;
         }
         return T_MISS;
     }
-    bool inside = E0 > st.tau[0] && E1 > st.tau[1] && E2 > st.tau[2];
+    bool inside = E0 > tau0 && E1 > tau1 && E2 > tau2;
     float adn = fabsf(dn);
-    t_err = st.err_det + (fabsf(d.x) * st.G[0] + fabsf(d.y) * st.G[1] + fabsf(d.z) * st.G[2]) / adn;
+    t_err = st.f(16) + (fabsf(d.x) * st.f(18) + fabsf(d.y) * st.f(19) + fabsf(d.z) * st.f(20)) / adn;
     if (!(t > 0.f) || !(t_err < 0.25f)) {
         t_err = 1.f;
         return (inside && !unc_pair && !(t > 0.f)) ? T_MISS : T_UNCERTAIN;
@@ -790,7 +827,7 @@ __device__ __forceinline__ void cull_rest(const CastArgs& a, const SensorDev& S,
     if (det == 0.f && !(RECHECK && det_unc)) return;  // origin in the plane: t = 0, never a hit
     c.inl += ncand;
     PairSetup st;
-    make_setup(S, T, w, p, det, err_det, st);
+    make_setup(S, T, w, p, det, err_det, SetupWriterAoS{st});
     const float2* azs = a.az_sc + S.az_off;
     const int n = (int)S.n_rays;
     const int r0 = imod(sp.u_lo, n);
@@ -801,7 +838,7 @@ __device__ __forceinline__ void cull_rest(const CastArgs& a, const SensorDev& S,
         for (int qq = 0; qq < sp.n_r; ++qq) {
             V3 d = ray_dir(chv, __ldg(&azs[i]));
             float t, terr;
-            int res = test_fp32<RECHECK>(st, S, d, t, terr);
+            int res = test_fp32<RECHECK>(SetupAoS{st}, S, d, t, terr);
             c.tests++;
             if (dump) dump_candidate(a, gbase + i, tri);
             c.hits += commit<RECHECK>(a, gbase + i, tri, res, t, terr, c.unc, c.ties);
@@ -947,7 +984,18 @@ __device__ __forceinline__ void flush_survivors(const CastArgs& a, CullAWarpSmem
     if (fill == 0) return;
     for (uint32_t s = lane; s < n_sensors; s += 32) W.hist[s] = 0;
     __syncwarp();
-    for (uint32_t q = lane; q < fill; q += 32) W.rank[q] = (uint16_t)atomicAdd(&W.hist[W.buf[q] >> 53], 1u);
+    for (uint32_t q0 = 0; q0 < fill; q0 += 32) {
+        // one shared atomic per distinct sensor among 32 entries
+        const uint32_t q = q0 + lane;
+        const bool v = q < fill;
+        const uint32_t sn = v ? (uint32_t)(W.buf[q] >> 53) : 0xFFFFu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, sn);
+        const uint32_t leader = __ffs(peers) - 1;
+        uint32_t b = 0;
+        if (v && lane == leader) b = atomicAdd(&W.hist[sn], (uint32_t)__popc(peers));
+        b = __shfl_sync(0xffffffffu, b, leader);
+        if (v) W.rank[q] = (uint16_t)(b + __popc(peers & ((1u << lane) - 1u)));
+    }
     __syncwarp();
     // exclusive prefix over the sensor counts (n_sensors <= 64: two per lane)
     uint32_t h0 = lane < n_sensors ? W.hist[lane] : 0u, h1 = lane + 32 < n_sensors ? W.hist[lane + 32] : 0u;
@@ -1054,7 +1102,8 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
 // the warp's prefix sums), so the tests run without lane divergence.
 // ---------------------------------------------------------------------------
 struct CullBWarpSmem {
-    PairSetup st[32];
+    float st[SETUP_FIELDS][32];  // field-major setups of the warp's 32 pairs
+    uint32_t cnt[8];             // live, cand, inl, big, tests, hits, unc, ties
 };
 template <bool RECHECK, bool BRUTE>
 __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
@@ -1063,13 +1112,15 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     CullBWarpSmem& W = reinterpret_cast<CullBWarpSmem*>(M.rest)[wib];
     const bool dump = a.flags & 16u;
-    CullCounters c;
+    if (lane < 8) W.cnt[lane] = 0;
+    uint32_t c_unc = 0, c_ties = 0;
     const uint32_t n = min(*(volatile uint32_t*)&a.qcount[Q_SURV], a.surv_cap);
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t gwarp = ((blockIdx.x * blockDim.x) >> 5) + wib;
     for (uint32_t b0 = gwarp * 32; b0 < n; b0 += n_warps * 32) {
         const uint32_t q = b0 + lane;
         uint32_t ncand = 0, my_tri = 0, my_meta = 0, my_r0 = 0;
+        uint32_t l_live = 0, l_cand = 0, l_big = 0;
         float my_inv = 0.f;
         if (q < n) {
             const unsigned long long r = __ldcs(&a.surv[q]);
@@ -1128,8 +1179,8 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
             }
             if (keep) {
                 const uint32_t nc = (uint32_t)(sp.j_hi - sp.j_lo + 1) * (uint32_t)sp.n_r;
-                c.live++;
-                c.cand += nc;
+                l_live = 1;
+                l_cand = nc;
                 if (!BRUTE && nc > a.inline_max) {
                     cg::coalesced_group grp = cg::coalesced_threads();
                     uint32_t bb = 0;
@@ -1150,7 +1201,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
                     } else {
                         atomicOr(a.error, (uint32_t)ERR_BIG_CAP);
                     }
-                    c.big++;
+                    l_big = 1;
                 } else {
                     TriW T;
                     tri_world(t9, T);
@@ -1158,13 +1209,13 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
                     float err_det = det_error(w[0], T);
                     bool det_unc = fabsf(det) <= err_det;
                     if (det != 0.f || (RECHECK && det_unc)) {
-                        make_setup(S, T, w, p, det, err_det, W.st[lane]);
+                        make_setup(S, T, w, p, det, err_det, SetupWriterSoA{&W.st[0][0], lane});
                         my_tri = tri;
                         my_meta = (uint32_t)sp.j_lo | ((uint32_t)sp.n_r << 10) | (sn << 26);
                         my_r0 = (uint32_t)imod(sp.u_lo, (int)S.n_rays);
                         my_inv = __frcp_ru((float)sp.n_r);
                         ncand = nc;
-                        c.inl += nc;
+
                     }
                 }
             }
@@ -1179,6 +1230,17 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
         const uint32_t excl = incl - ncand;
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         const uint32_t nz = __ballot_sync(0xffffffffu, ncand > 0);   // lanes that own candidates, in order
+        {
+            const uint32_t s_live = __reduce_add_sync(0xffffffffu, l_live), s_cand = __reduce_add_sync(0xffffffffu, l_cand),
+                           s_big = __reduce_add_sync(0xffffffffu, l_big);
+            if (lane == 0) {
+                W.cnt[0] += s_live;
+                W.cnt[1] += s_cand;
+                W.cnt[2] += total;
+                W.cnt[3] += s_big;
+                W.cnt[4] += total;
+            }
+        }
         __syncwarp();
         for (uint32_t c0 = 0; c0 < total; c0 += 32) {
             // rank (among owning lanes) of the pair holding candidate c0, and the
@@ -1194,6 +1256,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
             const uint32_t tri = __shfl_sync(0xffffffffu, my_tri, own & 31u);
             const float inv = __shfl_sync(0xffffffffu, my_inv, own & 31u);
             const uint32_t cc = c0 + lane;
+            uint32_t hit = 0;
             if (cc < total) {
                 const uint32_t nr = (meta >> 10) & 0xFFFFu;
                 const uint32_t sn = meta >> 26;
@@ -1215,15 +1278,26 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
                 const unsigned long long cur = __ldcg(&a.keys[g]);   // issued before the test arithmetic
                 V3 d = ray_dir(M.ch[S.ch_loc + j], __ldg(&a.az_sc[S.az_off + i]));
                 float t, terr;
-                int res = test_fp32<RECHECK>(W.st[own & 31u], S, d, t, terr);
-                c.tests++;
+                int res = test_fp32<RECHECK>(SetupSoA{&W.st[0][0], own & 31u}, S, d, t, terr);
                 if (dump) dump_candidate(a, g, tri);
-                c.hits += commit_pre<RECHECK>(a, g, tri, res, t, terr, cur, c.unc, c.ties);
+                hit = commit_pre<RECHECK>(a, g, tri, res, t, terr, cur, c_unc, c_ties);
             }
+            const uint32_t s_hits = __reduce_add_sync(0xffffffffu, hit);
+            if (lane == 0) W.cnt[5] += s_hits;
         }
         __syncwarp();
     }
-    c.flush(a);
+    c_unc = __reduce_add_sync(0xffffffffu, c_unc);
+    c_ties = __reduce_add_sync(0xffffffffu, c_ties);
+    __syncwarp();
+    if (lane == 0) {
+        const int idx[8] = {C_PAIRS_LIVE, C_CAND, C_CAND_INLINE, C_BIG, C_TESTS, C_HITS, C_UNCERTAIN, C_TIES};
+        W.cnt[6] = c_unc;
+        W.cnt[7] = c_ties;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (W.cnt[k]) atomicAdd(&a.counters[idx[k]], (unsigned long long)W.cnt[k]);
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_SURV] = *(volatile uint32_t*)&a.qcount[Q_SURV];
 }
 
@@ -1330,7 +1404,7 @@ __global__ void __launch_bounds__(256) k_expand(CastArgs a) {
         float err_det = det_error(w[0], T);
         if (lane == 0) {
             PairSetup st;
-            make_setup(S, T, w, p, det, err_det, st);
+            make_setup(S, T, w, p, det, err_det, SetupWriterAoS{st});
             a.setups[bp] = st;
         }
         float s_v[3];
@@ -1428,7 +1502,7 @@ __global__ void __launch_bounds__(256) k_test(CastArgs a) {
             if (i >= n) i -= n;
             V3 d = ray_dir(chv, __ldg(&a.az_sc[S.az_off + i]));
             float t, terr;
-            int res = test_fp32<RECHECK>(st, S, d, t, terr);
+            int res = test_fp32<RECHECK>(SetupAoS{st}, S, d, t, terr);
             c_tests++;
             if (dump) dump_candidate(a, gbase + i, tri);
             c_hits += commit<RECHECK>(a, gbase + i, tri, res, t, terr, c_unc, c_ties);
