@@ -563,7 +563,8 @@ __device__ __forceinline__ bool elev_range(const V3 p[3], float& smin, float& sm
 // Same bounds as elev_range; the vertical-axis test runs in the emitter frame
 // only when a necessary condition holds: the projected triangle can contain
 // the origin only if its nearest vertex lies within the longest edge of it.
-__device__ __forceinline__ bool elev_range_w(const SensorDev& S, const V3 w[3], float& smin, float& smax) {
+__device__ __forceinline__ bool elev_range_w(const SensorDev& S, const V3 w[3], const float eeT[3], float& smin,
+                                             float& smax) {
     const V3 u = {S.B[6], S.B[7], S.B[8]};
     float z[3], r2[3], sv[3];
 #pragma unroll
@@ -579,13 +580,17 @@ __device__ __forceinline__ bool elev_range_w(const SensorDev& S, const V3 w[3], 
     for (int k = 0; k < 3; ++k) {
         int k1 = k == 2 ? 0 : k + 1;
         V3 a = w[k];
-        V3 e = {w[k1].x - a.x, w[k1].y - a.y, w[k1].z - a.z};
-        float ee = e.x * e.x + e.y * e.y + e.z * e.z;
-        ee_max = fmaxf(ee_max, ee);
+        // upper bound of |w[k1]-w[k]|^2 from the world-frame edge E (sensor
+        // independent): |w[k1]-w[k]| <= |E|(1+u) + 4u|w|, so
+        // |w[k1]-w[k]|^2 <= 1.0001 |E|^2 + 1.6e5 (4u)^2 |w|^2 / 16
         float m2 = fminf(r2[k], r2[k1]);
+        float ee = 1.0001f * eeT[k] + 5.7e-10f * fmaxf(r2[k], r2[k1]);
+        ee_max = fmaxf(ee_max, ee);
         if (ee < 1e-5f * m2) {
             dev = fmaxf(dev, 0.31f * ee * __frcp_ru(m2));
         } else {
+            V3 e = {w[k1].x - a.x, w[k1].y - a.y, w[k1].z - a.z};
+            ee = e.x * e.x + e.y * e.y + e.z * e.z;
             // interior extremum of the edge's great circle: +-|m_h|/|m|, m = a x e
             float ez = z[k1] - z[k];
             float ae = a.x * e.x + a.y * e.y + a.z * e.z;
@@ -718,7 +723,7 @@ __device__ __forceinline__ uint32_t pack_span(int jl, int jh, bool pierced) {
 // the channel span from the elevation range.  Returns false when culled.
 template <bool RECHECK, bool BRUTE, typename T>
 __device__ __forceinline__ bool cull_elevation(const SensorDev& S, const T* ch, const uint16_t* lut, const V3 v[3],
-                                               const V3& nw, bool cull_back, uint32_t& span) {
+                                               const V3& nw, const float eeT[3], bool cull_back, uint32_t& span) {
     V3 w0 = rel_origin(S, v[0]);
     if (cull_back) {
         float det = vdot(w0, nw);
@@ -735,7 +740,7 @@ __device__ __forceinline__ bool cull_elevation(const SensorDev& S, const T* ch, 
     }
     const V3 wv[3] = {w0, rel_origin(S, v[1]), rel_origin(S, v[2])};
     float smin, smax;
-    bool pierced = elev_range_w(S, wv, smin, smax);
+    bool pierced = elev_range_w(S, wv, eeT, smin, smax);
     int jl = chan_lower(S, ch, lut, smin - EPS_S);
     if (jl >= (int)S.n_ch || sin_at(ch, jl) > smax + EPS_S) return false;  // no channel in the range
     int jh = chan_upper(S, ch, lut, smax + EPS_S) - 1;
@@ -914,6 +919,12 @@ __global__ void __launch_bounds__(256, 3) k_cull(CastArgs a) {
         V3 v[3] = {{t9[0], t9[1], t9[2]}, {t9[3], t9[4], t9[5]}, {t9[6], t9[7], t9[8]}};
         V3 nw = vcross(vsub(v[1], v[0]), vsub(v[2], v[0]));
         if (nw.x == 0.f && nw.y == 0.f && nw.z == 0.f) valid = false;  // zero area: never hit
+        float eeT[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            V3 e = vsub(v[k == 2 ? 0 : k + 1], v[k]);
+            eeT[k] = vdot(e, e);
+        }
         for (uint32_t sg = 0; sg < a.n_sensors; sg += CULL_GROUP) {
             const uint32_t ng = min((uint32_t)CULL_GROUP, a.n_sensors - sg);
             uint32_t mask = 0;
@@ -921,7 +932,7 @@ __global__ void __launch_bounds__(256, 3) k_cull(CastArgs a) {
                 for (uint32_t k = 0; k < ng; ++k) {
                     uint32_t span;
                     if (cull_elevation<RECHECK, BRUTE>(M.sens[sg + k], M.ch + M.sens[sg + k].ch_loc,
-                                                       M.lut + (sg + k) * LUT_BINS, v, nw, cull_back, span)) {
+                                                       M.lut + (sg + k) * LUT_BINS, v, nw, eeT, cull_back, span)) {
                         mask |= 1u << k;
                         W.span[lane * CULL_GROUP + k] = span;
                     }
@@ -1072,6 +1083,12 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
         V3 v[3] = {{t9[0], t9[1], t9[2]}, {t9[3], t9[4], t9[5]}, {t9[6], t9[7], t9[8]}};
         V3 nw = vcross(vsub(v[1], v[0]), vsub(v[2], v[0]));
         if (nw.x == 0.f && nw.y == 0.f && nw.z == 0.f) valid = false;  // zero area: never hit
+        float eeT[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            V3 e = vsub(v[k == 2 ? 0 : k + 1], v[k]);
+            eeT[k] = vdot(e, e);
+        }
         for (uint32_t sg = 0; sg < a.n_sensors; sg += CULL_A_GROUP) {
             const uint32_t ng = min((uint32_t)CULL_A_GROUP, a.n_sensors - sg);
             if (fill + 32 * CULL_A_GROUP > SURV_BUF) flush_survivors(a, W, fill, lane, a.n_sensors);
@@ -1079,7 +1096,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
                 uint32_t span = 0;
                 const SensorDev& S = M.sens[sg + k];
                 bool ok = valid && cull_elevation<RECHECK, BRUTE>(S, M.sins + S.ch_loc, M.lut + (sg + k) * LUT_BINS, v,
-                                                                  nw, cull_back, span);
+                                                                  nw, eeT, cull_back, span);
                 uint32_t bal = __ballot_sync(0xffffffffu, ok);
                 if (ok)
                     W.buf[fill + __popc(bal & ((1u << lane) - 1u))] =
@@ -1120,7 +1137,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
     for (uint32_t b0 = gwarp * 32; b0 < n; b0 += n_warps * 32) {
         const uint32_t q = b0 + lane;
         uint32_t ncand = 0, my_tri = 0, my_meta = 0, my_r0 = 0;
-        uint32_t l_live = 0, l_cand = 0, l_big = 0;
+        uint32_t l_live = 0, l_cand = 0, l_big = 0, hit0 = 0, tested0 = 0;
         float my_inv = 0.f;
         if (q < n) {
             const unsigned long long r = __ldcs(&a.surv[q]);
@@ -1214,8 +1231,17 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
                         my_meta = (uint32_t)sp.j_lo | ((uint32_t)sp.n_r << 10) | (sn << 26);
                         my_r0 = (uint32_t)imod(sp.u_lo, (int)S.n_rays);
                         my_inv = __frcp_ru((float)sp.n_r);
-                        ncand = nc;
-
+                        // the pair's first candidate is tested here by its own lane;
+                        // the remaining ones are expanded cooperatively below
+                        const uint32_t g = S.ray_off + (uint32_t)sp.j_lo * S.n_rays + my_r0;
+                        const unsigned long long cur = __ldcg(&a.keys[g]);
+                        V3 d = ray_dir(M.ch[S.ch_loc + sp.j_lo], __ldg(&a.az_sc[S.az_off + my_r0]));
+                        float t, terr;
+                        int res = test_fp32<RECHECK>(SetupSoA{&W.st[0][0], lane}, S, d, t, terr);
+                        if (dump) dump_candidate(a, g, tri);
+                        hit0 = commit_pre<RECHECK>(a, g, tri, res, t, terr, cur, c_unc, c_ties);
+                        tested0 = 1;
+                        ncand = nc - 1;
                     }
                 }
             }
@@ -1232,13 +1258,15 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
         const uint32_t nz = __ballot_sync(0xffffffffu, ncand > 0);   // lanes that own candidates, in order
         {
             const uint32_t s_live = __reduce_add_sync(0xffffffffu, l_live), s_cand = __reduce_add_sync(0xffffffffu, l_cand),
-                           s_big = __reduce_add_sync(0xffffffffu, l_big);
+                           s_big = __reduce_add_sync(0xffffffffu, l_big), s_t0 = __reduce_add_sync(0xffffffffu, tested0),
+                           s_h0 = __reduce_add_sync(0xffffffffu, hit0);
             if (lane == 0) {
                 W.cnt[0] += s_live;
                 W.cnt[1] += s_cand;
-                W.cnt[2] += total;
+                W.cnt[2] += total + s_t0;
                 W.cnt[3] += s_big;
-                W.cnt[4] += total;
+                W.cnt[4] += total + s_t0;
+                W.cnt[5] += s_h0;
             }
         }
         __syncwarp();
@@ -1260,7 +1288,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
             if (cc < total) {
                 const uint32_t nr = (meta >> 10) & 0xFFFFu;
                 const uint32_t sn = meta >> 26;
-                uint32_t idx = cc - o_excl;
+                uint32_t idx = cc - o_excl + 1;   // candidate 0 was tested by the owner lane
                 // quotient from the rounded-up reciprocal, then one correction
                 // step in each direction (idx < 2^24, so (float)idx is exact)
                 uint32_t jo = (uint32_t)((float)idx * inv);
@@ -1551,26 +1579,28 @@ __device__ unsigned long long test_fp64(const CastArgs& a, uint32_t g, uint32_t 
     D3 d = {ca * S.B64[0] + sa * S.B64[3] + su * S.B64[6], ca * S.B64[1] + sa * S.B64[4] + su * S.B64[7],
             ca * S.B64[2] + sa * S.B64[5] + su * S.B64[8]};
     const float* t9 = a.tris + 9ull * tri;
-    V3 vf[3];
-    D3 v[3], w[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        vf[k] = {t9[3 * k], t9[3 * k + 1], t9[3 * k + 2]};
-        v[k] = {(double)vf[k].x, (double)vf[k].y, (double)vf[k].z};
-        w[k] = {v[k].x - S.o64[0], v[k].y - S.o64[1], v[k].z - S.o64[2]};
-    }
-    D3 n = dcross(dsub(v[1], v[0]), dsub(v[2], v[0]));
+    const V3 f0 = {__ldg(t9 + 0), __ldg(t9 + 1), __ldg(t9 + 2)}, f1 = {__ldg(t9 + 3), __ldg(t9 + 4), __ldg(t9 + 5)},
+             f2 = {__ldg(t9 + 6), __ldg(t9 + 7), __ldg(t9 + 8)};
+    const D3 v0 = {(double)f0.x, (double)f0.y, (double)f0.z}, v1 = {(double)f1.x, (double)f1.y, (double)f1.z},
+             v2 = {(double)f2.x, (double)f2.y, (double)f2.z};
+    const D3 o = {S.o64[0], S.o64[1], S.o64[2]};
+    const D3 w0 = dsub(v0, o), w1 = dsub(v1, o), w2 = dsub(v2, o);
+    D3 n = dcross(dsub(v1, v0), dsub(v2, v0));
     if (n.x == 0.0 && n.y == 0.0 && n.z == 0.0) return KEY_MISS;
-    double det = ddot(w[0], n);
+    double det = ddot(w0, n);
     if (det == 0.0) return KEY_MISS;
     if ((a.flags & 2u) && det > 0.0) return KEY_MISS;  // back-facing
     double fold = det < 0.0 ? -1.0 : 1.0;
+    // canonical edge functions (same rule as the FP32 test): base = the
+    // lexicographically smaller vertex, evaluated from it; selects, no arrays
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        int k1 = k == 2 ? 0 : k + 1;
-        bool fwd = !lex_less(vf[k1], vf[k]);
-        int b = fwd ? k : k1, o = fwd ? k1 : k;
-        D3 m = dcross(w[b], dsub(v[o], v[b]));
+        const V3 fa = k == 0 ? f0 : (k == 1 ? f1 : f2), fb = k == 0 ? f1 : (k == 1 ? f2 : f0);
+        const D3 va = k == 0 ? v0 : (k == 1 ? v1 : v2), vb = k == 0 ? v1 : (k == 1 ? v2 : v0);
+        const D3 wa = k == 0 ? w0 : (k == 1 ? w1 : w2), wb = k == 0 ? w1 : (k == 1 ? w2 : w0);
+        const bool fwd = !lex_less(fb, fa);
+        const D3 wbase = fwd ? wa : wb, vbase = fwd ? va : vb, voth = fwd ? vb : va;
+        const D3 m = dcross(wbase, dsub(voth, vbase));
         double E = ddot(d, m) * (fwd ? fold : -fold);
         if (E < 0.0) return KEY_MISS;
     }
