@@ -70,7 +70,13 @@ enum {
     GRCA_CAST_GRAPH = 1u << 3,
     /* Debug: append every tested (ray, triangle) candidate to the dump buffer
      * set by grca_set_debug_dump (for superset checks of the culling). */
-    GRCA_CAST_DUMP_CANDIDATES = 1u << 4
+    GRCA_CAST_DUMP_CANDIDATES = 1u << 4,
+    /* Lossy apparent-area cull (App. A.4.1 Step 1, Eq. apparent_area): skip a
+     * (triangle, sensor) pair when (A_T (c-o).n^)^2 < eps_A^2 |c-o|^6, with
+     * A_T the area, c the centroid and n^ the unit normal; eps_A =
+     * grca_options.area_eps (default 1e-6, the paper's value).  Drops true
+     * hits on small, far or edge-on triangles by design. */
+    GRCA_CAST_LOSSY_AREA = 1u << 5
 };
 
 /* Context options (all fields 0 = library default). */
@@ -84,6 +90,7 @@ typedef struct {
     uint32_t cull_blocks_per_sm; /* resident culling blocks per SM (default 4) */
     uint64_t survivor_capacity;  /* max (triangle, sensor) pairs passing the elevation cull per cast
                                     (default 256M, 8 B each; the queue grows to n_tris * n_sensors up to it) */
+    double area_eps;             /* eps_A of GRCA_CAST_LOSSY_AREA (default 1e-6) */
 } grca_options;
 
 /* One spinning LiDAR (Sec. 3.1, Eq. ray_dir and the centred angle grid).
@@ -184,6 +191,39 @@ grca_status grca_cast_host(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_
  * the best frame time. */
 grca_status grca_autotune(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_sensors, float* out_dist,
                           uint32_t* out_tri, uint32_t flags, void* stream, float* out_ms);
+
+/* Non-spinning and patterned sensors (App. A.3, animated ray-mask images):
+ * an on/off mask over the sensor's channel x ray grid.  `bits` holds
+ * ceil(n_channels*n_rays/32) uint32 words; bit (q & 31) of word q >> 5, with
+ * q = j*n_rays + i, set = ray (j, i) fires.  Rays that do not fire report a
+ * miss (+inf, 0xFFFFFFFF) at their usual, stable output index.  `where` =
+ * GRCA_MEM_HOST (copied before return) or GRCA_MEM_DEVICE (copied on
+ * `stream`; the source may be reused once that stream reaches the copy).
+ * bits = NULL removes the mask.  Call again between casts to animate it.
+ * Returns GRCA_ERR_INVALID_ARG for a bad id or `where`. */
+grca_status grca_set_ray_mask(grca_ctx* ctx, int32_t sensor_id, const uint32_t* bits, int where, void* stream);
+
+/* Horizontal angular noise (App. A.1, Eq. noise_search): per-ray azimuths
+ * theta[i] (radians, n_rays host doubles, copied) that replace theta0 +
+ * i*dtheta, each strictly within dtheta of its nominal value so that the
+ * search window of a ray stays its nominal index +-1.  Spans widen by the
+ * largest perturbation; the ray tests use the perturbed directions.
+ * theta = NULL restores the uniform grid.  Returns GRCA_ERR_INVALID_ARG when
+ * a value is not finite or lies dtheta or more from its nominal azimuth.
+ * (Per-channel vertical noise needs no call: give the perturbed, still
+ * ascending elevations as the sensor's elevation table.) */
+grca_status grca_set_sensor_azimuths(grca_ctx* ctx, int32_t sensor_id, const double* theta);
+
+/* Range noise (App. A.1, applied after output conversion): each hit
+ * distance of the sensor gets sigma * z added, with z = sqrt(-2 ln u1)
+ * cos(2 pi u2) (Box and Muller, 1958), u1 = (hi24(a) + 1) / 2^24,
+ * u2 = hi24(b) / 2^24, a = splitmix64(seed + 2q), b = splitmix64(seed + 2q + 1),
+ * q = j*n_rays + i the ray's index within the sensor, hi24 the top 24 bits
+ * and splitmix64 the output function of SplitMix64 (Steele, Lea and Flood,
+ * 2014) for the state x: mix(x + 0x9E3779B97F4A7C15).  z is evaluated in
+ * FP32.  sigma = 0 turns it off; change the seed per frame for fresh noise.
+ * Returns GRCA_ERR_INVALID_ARG for a bad id or a negative or non-finite sigma. */
+grca_status grca_set_range_noise(grca_ctx* ctx, int32_t sensor_id, double sigma, uint64_t seed);
 
 /* Allocation-free cast of one sensor.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc (for example

@@ -38,9 +38,10 @@ static void load_tri(const float* tri, double v0[3], double v1[3], double v2[3])
     }
 }
 
-/* Eq. ray_dir (Sec. 3.1): d = cos(th)cos(ph) f + sin(th)cos(ph) r + sin(ph) u. */
+/* Eq. ray_dir (Sec. 3.1): d = cos(th)cos(ph) f + sin(th)cos(ph) r + sin(ph) u;
+ * th is the ray's own azimuth when the sensor lists perturbed ones (App. A.1). */
 void orc_ray_dir(const orc_sensor* s, uint32_t j, uint32_t i, double d[3]) {
-    double th = s->theta0 + (double)i * s->dtheta;
+    double th = s->theta ? s->theta[i] : s->theta0 + (double)i * s->dtheta;
     double ph = s->elev[j];
     double a = cos(th) * cos(ph), b = sin(th) * cos(ph), c = sin(ph);
     for (int k = 0; k < 3; ++k) d[k] = a * s->f[k] + b * s->r[k] + c * s->u[k];
@@ -119,6 +120,7 @@ typedef struct {
     uint32_t* tie_ids;
     uint64_t tests;
     int error;
+    const uint8_t* keep;
 } cast_job;
 
 static int ray_tri(const orc_sensor* s, const double d[3], const float* tri, int cull, double* t) {
@@ -139,12 +141,23 @@ static void* cast_worker(void* arg) {
             return NULL;
         }
         const orc_sensor* s = &jb->sensors[sn];
+        const uint64_t q = (uint64_t)j * s->n_rays + i;
+        if (s->mask && !((s->mask[q >> 5] >> (q & 31u)) & 1u)) {
+            /* the ray does not fire (App. A.3): a miss */
+            jb->best_t[r] = INFINITY;
+            jb->best_id[r] = ORC_NO_HIT;
+            if (jb->second_t) jb->second_t[r] = INFINITY;
+            if (jb->n_ties) jb->n_ties[r] = 0;
+            continue;
+        }
         double d[3];
         orc_ray_dir(s, j, i, d);
         double best = INFINITY;
         uint32_t bid = ORC_NO_HIT;
+        const uint8_t* keep = jb->keep ? jb->keep + (size_t)sn * jb->n_tris : NULL;
         for (uint32_t k = 0; k < jb->n_tris; ++k) {
             double t;
+            if (keep && !keep[k]) continue;
             if (ray_tri(s, d, jb->tris + 9 * (size_t)k, jb->cull_backface, &t) && t < best) {
                 best = t;
                 bid = k;  /* strict '<' over ascending k: ties keep the lower id */
@@ -160,6 +173,7 @@ static void* cast_worker(void* arg) {
             double lim = best * (1.0 + jb->tie_rel);
             for (uint32_t k = 0; k < jb->n_tris; ++k) {
                 double t;
+                if (keep && !keep[k]) continue;
                 if (!ray_tri(s, d, jb->tris + 9 * (size_t)k, jb->cull_backface, &t)) continue;
                 if (k != bid && t < second) second = t;
                 if (bid != ORC_NO_HIT && t <= lim) {
@@ -177,7 +191,7 @@ static void* cast_worker(void* arg) {
 int orc_cast(const orc_sensor* sensors, uint32_t n_sensors, const float* tris, uint32_t n_tris,
              const int64_t* ray_ids, int64_t n_rays, int cull_backface, double tie_rel, int n_threads,
              double* best_t, uint32_t* best_id, double* second_t, uint32_t* n_ties, uint32_t* tie_ids,
-             uint64_t* n_tests) {
+             uint64_t* n_tests, const uint8_t* keep) {
     if (!sensors || !n_sensors || (!tris && n_tris) || (!ray_ids && n_rays) || !best_t || !best_id)
         return -1;
     if (n_threads < 1) n_threads = 1;
@@ -205,6 +219,7 @@ int orc_cast(const orc_sensor* sensors, uint32_t n_sensors, const float* tris, u
         jb->second_t = second_t;
         jb->n_ties = n_ties;
         jb->tie_ids = tie_ids;
+        jb->keep = keep;
     }
     for (int w = 1; w < n_threads; ++w) pthread_create(&th[w], NULL, cast_worker, &jobs[w]);
     cast_worker(&jobs[0]);
@@ -219,6 +234,32 @@ int orc_cast(const orc_sensor* sensors, uint32_t n_sensors, const float* tris, u
     free(jobs);
     free(th);
     return err ? -1 : 0;
+}
+
+/* Eq. apparent_area (App. A.4.1 Step 1): A_origin = A_T (c-o).n^ / |c-o|^3,
+ * compared squared: (A_T (c-o).n^)^2 < eps^2 |c-o|^6 drops the pair. */
+void orc_area_keep(const orc_sensor* sensors, uint32_t n_sensors, const float* tris, uint32_t n_tris, double eps,
+                   uint8_t* out) {
+    for (uint32_t n = 0; n < n_sensors; ++n) {
+        const orc_sensor* s = &sensors[n];
+        for (uint32_t k = 0; k < n_tris; ++k) {
+            double v0[3], v1[3], v2[3], e1[3], e2[3], nrm[3], c[3];
+            load_tri(tris + 9 * (size_t)k, v0, v1, v2);
+            sub3(v1, v0, e1);
+            sub3(v2, v0, e2);
+            cross3(e1, e2, nrm);
+            double len = sqrt(dot3(nrm, nrm));
+            double area = 0.5 * len;
+            for (int i = 0; i < 3; ++i) c[i] = (v0[i] + v1[i] + v2[i]) / 3.0 - s->origin[i];
+            double cn = len > 0.0 ? dot3(c, nrm) / len : 0.0;
+            double lhs = (area * cn) * (area * cn);
+            double r2 = dot3(c, c);
+            double rhs = eps * eps * r2 * r2 * r2;
+            uint8_t v = lhs < rhs ? 0 : 1;
+            if (fabs(lhs - rhs) <= 1e-3 * rhs) v = 2;
+            out[(size_t)n * n_tris + k] = v;
+        }
+    }
 }
 
 int orc_ray_tri_margin(const orc_sensor* sensors, uint32_t n_sensors, int64_t ray_id,
@@ -339,4 +380,23 @@ int64_t orc_triangle_hits(const orc_sensor* s, const float* tris, uint32_t n_tri
     free(jobs);
     free(th);
     return counter;
+}
+
+uint64_t orc_splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+#define ORC_PI 3.14159265358979323846
+
+void orc_range_noise(uint64_t seed, const int64_t* q, int64_t n, double* z) {
+    const double two24 = 16777216.0;
+    for (int64_t k = 0; k < n; ++k) {
+        uint64_t c = seed + 2ull * (uint64_t)q[k];
+        double u1 = ((double)(orc_splitmix64(c) >> 40) + 1.0) / two24;
+        double u2 = (double)(orc_splitmix64(c + 1ull) >> 40) / two24;
+        z[k] = sqrt(-2.0 * log(u1)) * cos(2.0 * ORC_PI * u2);
+    }
 }

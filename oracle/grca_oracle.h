@@ -40,9 +40,15 @@ typedef struct {
     const double* elev;        /* n_channels elevations (radians) */
     uint32_t n_channels;
     uint32_t n_rays;
+    const double* theta;       /* nullable: n_rays per-ray azimuths replacing theta0 + i*dtheta
+                                  (horizontal noise, App. A.1) */
+    const uint32_t* mask;      /* nullable: ray (j, i) fires iff bit q & 31 of mask[q >> 5] is set,
+                                  q = j*n_rays + i (ray-mask images, App. A.3); a ray that does
+                                  not fire is a miss */
 } orc_sensor;
 
-/* Ray direction of (channel j, ray i): Eq. ray_dir. */
+/* Ray direction of (channel j, ray i): Eq. ray_dir, with theta[i] in place
+ * of theta0 + i*dtheta when the sensor has per-ray azimuths. */
 void orc_ray_dir(const orc_sensor* s, uint32_t j, uint32_t i, double d[3]);
 
 /* One ray against one triangle (9 floats: v0, v1, v2).  Returns 1 and *t on
@@ -65,7 +71,29 @@ int orc_cast(const orc_sensor* sensors, uint32_t n_sensors,
              int cull_backface, double tie_rel, int n_threads,
              double* best_t, uint32_t* best_id,
              double* second_t, uint32_t* n_ties, uint32_t* tie_ids,
-             uint64_t* n_tests);
+             uint64_t* n_tests, const uint8_t* keep);
+/* keep (nullable): n_sensors x n_tris bytes; triangle k is ignored for the
+ * rays of sensor n when keep[n * n_tris + k] == 0. */
+
+/* Apparent-area filter of App. A.4.1 Step 1 (Eq. apparent_area): for every
+ * (sensor n, triangle k), with A_T the area, c the centroid and n^ the unit
+ * normal, the pair is dropped when (A_T (c-o).n^)^2 < eps^2 |c-o|^6.
+ * out[n * n_tris + k] = 1 keep, 0 drop, 2 keep but within a relative 1e-3 of
+ * the threshold (where an FP32 evaluation may decide either way). */
+void orc_area_keep(const orc_sensor* sensors, uint32_t n_sensors, const float* tris, uint32_t n_tris, double eps,
+                   uint8_t* out);
+
+/* Range noise (App. A.1: added to the distance after output conversion):
+ * z[k] = sqrt(-2 ln u1) cos(2 pi u2), the Box-Muller transform (Box and
+ * Muller, 1958) of u1 = (top24(a) + 1) / 2^24 and u2 = top24(b) / 2^24, where
+ * a = sm(seed + 2 q[k]), b = sm(seed + 2 q[k] + 1) and sm(x) is the SplitMix64
+ * output for state x (Steele, Lea and Flood, 2014): x + 0x9E3779B97F4A7C15,
+ * then the two xor-shift-multiply rounds and a final xor-shift.  q is the
+ * ray's index j*n_rays + i within its sensor.  Arithmetic in FP64. */
+void orc_range_noise(uint64_t seed, const int64_t* q, int64_t n, double* z);
+
+/* The SplitMix64 output function sm(x) above (exposed for its published test vectors). */
+uint64_t orc_splitmix64(uint64_t x);
 
 /* Grading helper for one (ray, triangle): t of the ray with the triangle's
  * plane (+inf if parallel or degenerate) and the signed angular margin of the

@@ -44,7 +44,8 @@ class _Sensor(ctypes.Structure):
                 ("u", ctypes.c_double * 3), ("theta0", ctypes.c_double), ("dtheta", ctypes.c_double),
                 ("d_min", ctypes.c_double), ("d_max", ctypes.c_double),
                 ("elev", ctypes.POINTER(ctypes.c_double)), ("n_channels", ctypes.c_uint32),
-                ("n_rays", ctypes.c_uint32)]
+                ("n_rays", ctypes.c_uint32), ("theta", ctypes.POINTER(ctypes.c_double)),
+                ("mask", ctypes.POINTER(ctypes.c_uint32))]
 
 
 def load_library(path: str):
@@ -52,7 +53,9 @@ def load_library(path: str):
     lib = ctypes.CDLL(path)
     P = ctypes.c_void_p
     lib.orc_cast.argtypes = [P, ctypes.c_uint32, P, ctypes.c_uint32, P, ctypes.c_int64, ctypes.c_int,
-                             ctypes.c_double, ctypes.c_int, P, P, P, P, P, P]
+                             ctypes.c_double, ctypes.c_int, P, P, P, P, P, P, P]
+    lib.orc_area_keep.argtypes = [P, ctypes.c_uint32, P, ctypes.c_uint32, ctypes.c_double, P]
+    lib.orc_area_keep.restype = None
     lib.orc_cast.restype = ctypes.c_int
     lib.orc_ray_dir.argtypes = [P, ctypes.c_uint32, ctypes.c_uint32, P]
     lib.orc_ray_dir.restype = None
@@ -60,6 +63,10 @@ def load_library(path: str):
     lib.orc_ray_tri_margin.restype = ctypes.c_int
     lib.orc_triangle_hits.argtypes = [P, P, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, P, ctypes.c_int64]
     lib.orc_triangle_hits.restype = ctypes.c_int64
+    lib.orc_range_noise.argtypes = [ctypes.c_uint64, P, ctypes.c_int64, P]
+    lib.orc_range_noise.restype = None
+    lib.orc_splitmix64.argtypes = [ctypes.c_uint64]
+    lib.orc_splitmix64.restype = ctypes.c_uint64
     lib.orc_hit.argtypes = [P, P, P, P]
     lib.orc_hit.restype = ctypes.c_int
     return lib
@@ -75,11 +82,17 @@ def _load():
 
 
 class Oracle:
-    """Holds ctypes copies of a sensor list (keeps the elevation arrays alive)."""
+    """Holds ctypes copies of a sensor list (keeps the elevation, azimuth and
+    mask arrays alive).  masks: optional per-sensor uint32 on/off words (None
+    entries: every ray fires); per-ray azimuths come from `s.azimuths`."""
 
-    def __init__(self, sensors: Sequence, lib=None):
+    def __init__(self, sensors: Sequence, lib=None, masks: Optional[Sequence] = None):
         self.lib = lib if lib is not None else _load()
         self._elev = [np.ascontiguousarray(s.elev, dtype=np.float64) for s in sensors]
+        self._theta = [None if getattr(s, "azimuths", None) is None else
+                       np.ascontiguousarray(s.azimuths, dtype=np.float64) for s in sensors]
+        self._mask = [None if masks is None or masks[k] is None else
+                      np.ascontiguousarray(masks[k], dtype=np.uint32) for k in range(len(sensors))]
         arr = (_Sensor * len(sensors))()
         for k, s in enumerate(sensors):
             c = arr[k]
@@ -95,6 +108,12 @@ class Oracle:
             c.elev = self._elev[k].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             c.n_channels = int(s.elev.shape[0])
             c.n_rays = int(s.n_rays)
+            if self._theta[k] is not None:
+                assert self._theta[k].shape[0] == c.n_rays
+                c.theta = self._theta[k].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            if self._mask[k] is not None:
+                assert self._mask[k].shape[0] * 32 >= c.n_rays * c.n_channels
+                c.mask = self._mask[k].ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
         self.sensors = arr
         self.n = len(sensors)
 
@@ -107,8 +126,10 @@ def _threads(n: Optional[int]) -> int:
 
 
 def cast(sensors, tris: np.ndarray, ray_ids: Optional[np.ndarray] = None, cull_backface: bool = False,
-         ties: bool = False, tie_rel: float = 1e-6, n_threads: Optional[int] = None) -> dict:
-    """Brute-force closest hit of the listed global rays (all rays if None)."""
+         ties: bool = False, tie_rel: float = 1e-6, n_threads: Optional[int] = None,
+         keep: Optional[np.ndarray] = None) -> dict:
+    """Brute-force closest hit of the listed global rays (all rays if None).
+    keep: optional [n_sensors, n_tris] mask; 0 hides a triangle from that sensor."""
     o = sensors if isinstance(sensors, Oracle) else Oracle(sensors)
     tris = np.ascontiguousarray(tris, dtype=np.float32).reshape(-1, 9)
     if ray_ids is None:
@@ -122,15 +143,41 @@ def cast(sensors, tris: np.ndarray, ray_ids: Optional[np.ndarray] = None, cull_b
     n_ties = np.empty(n, np.uint32) if ties else None
     tie_ids = np.full((n, MAX_TIES), NO_HIT, np.uint32) if ties else None
     tests = np.zeros(1, np.uint64)
+    if keep is not None:
+        keep = np.ascontiguousarray(keep, dtype=np.uint8).reshape(o.n, tris.shape[0])
     p = lambda a: None if a is None else a.ctypes.data
     rc = o.lib.orc_cast(ctypes.byref(o.sensors), o.n, tris.ctypes.data, tris.shape[0], ray_ids.ctypes.data, n,
                         int(bool(cull_backface)), float(tie_rel), _threads(n_threads), best_t.ctypes.data,
-                        best_id.ctypes.data, p(second), p(n_ties), p(tie_ids), tests.ctypes.data)
+                        best_id.ctypes.data, p(second), p(n_ties), p(tie_ids), tests.ctypes.data, p(keep))
     if rc != 0:
         raise ValueError("orc_cast failed (bad ray id or argument)")
     out = {"t": best_t, "id": best_id, "tests": int(tests[0]), "ray_ids": ray_ids}
     if ties:
         out.update(second=second, n_ties=n_ties, tie_ids=tie_ids)
+    return out
+
+
+def range_noise(seed: int, q: np.ndarray, lib=None) -> np.ndarray:
+    """Standard normal range-noise draws z for sensor-local ray indices q (FP64)."""
+    lib = lib if lib is not None else _load()
+    q = np.ascontiguousarray(q, dtype=np.int64)
+    z = np.empty(q.shape[0], np.float64)
+    lib.orc_range_noise(int(seed) & (2**64 - 1), q.ctypes.data, q.shape[0], z.ctypes.data)
+    return z
+
+
+def splitmix64(x: int, lib=None) -> int:
+    lib = lib if lib is not None else _load()
+    return int(lib.orc_splitmix64(int(x) & (2**64 - 1)))
+
+
+def area_keep(sensors, tris: np.ndarray, eps: float = 1e-6) -> np.ndarray:
+    """[n_sensors, n_tris] uint8: 1 keep, 0 drop, 2 keep within 1e-3 of the threshold
+    (the apparent-area filter of App. A.4.1 Step 1)."""
+    o = sensors if isinstance(sensors, Oracle) else Oracle(sensors)
+    tris = np.ascontiguousarray(tris, dtype=np.float32).reshape(-1, 9)
+    out = np.empty((o.n, tris.shape[0]), np.uint8)
+    o.lib.orc_area_keep(ctypes.byref(o.sensors), o.n, tris.ctypes.data, tris.shape[0], float(eps), out.ctypes.data)
     return out
 
 
@@ -180,5 +227,6 @@ def hit(o3, d3, tri, lib=None) -> Optional[float]:
     return t.value if lib.orc_hit(o3.ctypes.data, d3.ctypes.data, tri.ctypes.data, ctypes.byref(t)) else None
 
 
-__all__ = ["MAX_TIES", "NO_HIT", "Oracle", "build_oracle", "cast", "compile_oracle", "hit", "load_library",
-           "ray_dirs", "ray_tri_margin", "triangle_hits"]
+__all__ = ["MAX_TIES", "NO_HIT", "Oracle", "area_keep", "build_oracle", "cast", "compile_oracle", "hit",
+           "range_noise", "splitmix64",
+           "load_library", "ray_dirs", "ray_tri_margin", "triangle_hits"]

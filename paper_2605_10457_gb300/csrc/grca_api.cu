@@ -28,7 +28,11 @@ constexpr int RING = 64;  // pinned staging slots for per-cast sensor descriptor
 struct SensorHost {
     grca_sensor_desc d;
     std::vector<double> elev;
+    std::vector<double> theta;   // per-ray azimuths (empty: uniform grid)
     bool full;
+    uint32_t* d_mask = nullptr;  // device on/off bits (nullptr: every ray fires)
+    double range_sigma = 0.0;
+    uint64_t noise_seed = 0;
 };
 
 struct GraphKey {
@@ -233,6 +237,7 @@ grca_status grca_create(grca_ctx** out, int device, const grca_options* opt) {
     if (!o.cull_block) o.cull_block = 256;
     if (!o.cull_blocks_per_sm) o.cull_blocks_per_sm = 4;
     if (!o.survivor_capacity) o.survivor_capacity = 256u << 20;
+    if (!(o.area_eps > 0.0)) o.area_eps = 1e-6;
     if (o.big_pair_capacity > 0xFFFFFFFFull || o.chunk_capacity > 0xFFFFFFFFull || o.recheck_capacity > 0xFFFFFFFFull ||
         o.survivor_capacity > 0xFFFFFFFFull ||
         o.cull_block % 32 || o.cull_block > 256 || o.cull_block < 32 || o.chunk_rays > 4096) {
@@ -297,6 +302,7 @@ void grca_destroy(grca_ctx* ctx) {
     if (ctx->cap_stream) cudaStreamSynchronize(ctx->cap_stream);
     cudaDeviceSynchronize();
     free_graphs(ctx);
+    for (SensorHost& sh : ctx->sensors) cudaFree(sh.d_mask);
     cudaFree(ctx->d_tris);
     cudaFree(ctx->d_ch);
     cudaFree(ctx->d_ch64);
@@ -405,6 +411,54 @@ grca_status grca_update_vertices(grca_ctx* ctx, const float* xyz, uint32_t first
     return copy_in(ctx, ctx->d_tris + 9ull * first, xyz, 9ull * n_tris, where, (cudaStream_t)stream);
 }
 
+grca_status grca_set_ray_mask(grca_ctx* ctx, int32_t id, const uint32_t* bits, int where, void* stream) {
+    if (!ctx || id < 0 || id >= (int32_t)ctx->sensors.size() || (where != GRCA_MEM_HOST && where != GRCA_MEM_DEVICE))
+        return GRCA_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    SensorHost& h = ctx->sensors[id];
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!bits) {
+        if (h.d_mask) {
+            // casts already queued may still read the mask
+            CK(cudaDeviceSynchronize());
+            cudaFree(h.d_mask);
+            h.d_mask = nullptr;
+        }
+        return GRCA_OK;
+    }
+    size_t words = ((size_t)h.d.n_channels * h.d.n_rays + 31) / 32;
+    if (!h.d_mask) CK(cudaMalloc(&h.d_mask, sizeof(uint32_t) * words));
+    CK(cudaMemcpyAsync(h.d_mask, bits, sizeof(uint32_t) * words,
+                       where == GRCA_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (where == GRCA_MEM_HOST) CK(cudaStreamSynchronize(st));
+    return GRCA_OK;
+}
+
+grca_status grca_set_sensor_azimuths(grca_ctx* ctx, int32_t id, const double* theta) {
+    if (!ctx || id < 0 || id >= (int32_t)ctx->sensors.size()) return GRCA_ERR_INVALID_ARG;
+    SensorHost& h = ctx->sensors[id];
+    if (!theta) {
+        if (h.theta.empty()) return GRCA_OK;
+        h.theta.clear();
+    } else {
+        for (uint32_t i = 0; i < h.d.n_rays; ++i) {
+            double nominal = h.d.theta0 + (double)i * h.d.dtheta;
+            if (!std::isfinite(theta[i]) || !(std::fabs(theta[i] - nominal) < h.d.dtheta)) return GRCA_ERR_INVALID_ARG;
+        }
+        h.theta.assign(theta, theta + h.d.n_rays);
+    }
+    ctx->tables_dirty = true;
+    return GRCA_OK;
+}
+
+grca_status grca_set_range_noise(grca_ctx* ctx, int32_t id, double sigma, uint64_t seed) {
+    if (!ctx || id < 0 || id >= (int32_t)ctx->sensors.size() || !std::isfinite(sigma) || !(sigma >= 0.0))
+        return GRCA_ERR_INVALID_ARG;
+    ctx->sensors[id].range_sigma = sigma;
+    ctx->sensors[id].noise_seed = seed;
+    return GRCA_OK;
+}
+
 grca_status grca_set_debug_dump(grca_ctx* ctx, uint32_t* pairs, uint64_t cap, uint32_t* counter) {
     if (!ctx) return GRCA_ERR_INVALID_ARG;
     if ((pairs == nullptr) != (counter == nullptr) || cap > 0xFFFFFFFFull) return GRCA_ERR_INVALID_ARG;
@@ -447,7 +501,7 @@ static grca_status ensure_tables(grca_ctx* ctx, cudaStream_t st) {
         ctx->lut_inv_w.push_back(iw);
         ctx->az_off.push_back((uint32_t)az.size());
         for (uint32_t i = 0; i < s.d.n_rays; ++i) {
-            double th = s.d.theta0 + (double)i * s.d.dtheta;
+            double th = s.theta.empty() ? s.d.theta0 + (double)i * s.d.dtheta : s.theta[i];
             double sn = std::sin(th), cs = std::cos(th);
             az.push_back(make_float2((float)sn, (float)cs));
             az64.push_back(make_double2(sn, cs));
@@ -533,12 +587,20 @@ static void fill_sensor(const grca_ctx* ctx, int id, uint32_t ray_off, SensorDev
     s.lut_lo = ctx->lut_lo[id];
     s.lut_inv_w = ctx->lut_inv_w[id];
     s.lut_off = (uint32_t)id * LUT_BINS;
+    double maxdev = 0.0;
+    for (size_t i = 0; i < h.theta.size(); ++i)
+        maxdev = std::max(maxdev, std::fabs(h.theta[i] - (d.theta0 + (double)i * d.dtheta)));
+    // span widening by the largest perturbation, in ray units, plus rounding slack
+    s.az_noise_pad = h.theta.empty() ? 0.f : (float)(maxdev / d.dtheta) + 1e-3f;
+    s.mask = h.d_mask;
+    s.noise_seed = h.noise_seed;
+    s.range_sigma = (float)h.range_sigma;
 }
 
 static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, float* out_dist, uint32_t* out_tri,
                                 uint32_t flags, cudaStream_t st, CastArgs& a) {
     if (!ids || n < 1 || n > (uint32_t)MAX_SENSORS || !out_dist || !out_tri) return GRCA_ERR_INVALID_ARG;
-    if (flags & ~0x1Fu) return GRCA_ERR_INVALID_ARG;
+    if (flags & ~0x3Fu) return GRCA_ERR_INVALID_ARG;
     if ((flags & GRCA_CAST_DUMP_CANDIDATES) && !ctx->dump) return GRCA_ERR_INVALID_ARG;
     for (uint32_t k = 0; k < n; ++k)
         if (ids[k] < 0 || ids[k] >= (int32_t)ctx->sensors.size()) return GRCA_ERR_INVALID_ARG;
@@ -580,6 +642,9 @@ static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, f
         off += ctx->sensors[ids[k]].d.n_channels * ctx->sensors[ids[k]].d.n_rays;
         ch_loc += ctx->sensors[ids[k]].d.n_channels;
     }
+    uint32_t post = 0;
+    for (uint32_t k = 0; k < n; ++k)
+        if (h[k].mask || h[k].range_sigma > 0.f) post = 1;
     CK(cudaMemcpyAsync(ctx->d_sens, h, sizeof(SensorDev) * n, cudaMemcpyHostToDevice, st));
     CK(cudaEventRecord(ctx->ring_ev[slot], st));
     ctx->ring_used[slot] = true;
@@ -619,11 +684,13 @@ static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, f
     a.out_tri = out_tri;
     a.surv = ctx->d_surv;
     a.surv_cap = (uint32_t)ctx->surv_cap;
+    a.area_eps2 = (float)(ctx->opt.area_eps * ctx->opt.area_eps);
+    a.post = post;
     return GRCA_OK;
 }
 
 static LaunchCfg cfg_for(grca_ctx* ctx, const CastArgs& a) {
-    auto key = std::make_tuple(a.n_sensors, a.n_rays_total, a.n_tris, a.flags & 0x7u);
+    auto key = std::make_tuple(a.n_sensors, a.n_rays_total, a.n_tris, a.flags & 0x27u);
     auto it = ctx->tuned.find(key);
     return it == ctx->tuned.end() ? ctx->cfg : it->second;
 }
@@ -642,7 +709,7 @@ static grca_status run_frame(grca_ctx* ctx, CastArgs& a, const LaunchCfg& cfg, c
         CK(cudaGetLastError());
         return GRCA_OK;
     }
-    GraphKey k{a.n_sensors, a.n_rays_total, a.total_ch, a.flags, a.n_tris, a.out_dist, a.out_tri, a.tris, a.keys,
+    GraphKey k{a.n_sensors, a.n_rays_total, a.total_ch, a.flags | (a.post ? 0x80000000u : 0u), a.n_tris, a.out_dist, a.out_tri, a.tris, a.keys,
                a.dump, cfg.cull_block, cfg.cull_blocks_per_sm, cfg.inline_max, cfg.chunk_rays};
     auto it = ctx->graphs.find(k);
     if (it == ctx->graphs.end()) {
@@ -836,7 +903,7 @@ grca_status grca_autotune(grca_ctx* ctx, const int32_t* ids, uint32_t n, float* 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rs != GRCA_OK) return rs;
-    ctx->tuned[std::make_tuple(a.n_sensors, a.n_rays_total, a.n_tris, fl & 0x7u)] = best;
+    ctx->tuned[std::make_tuple(a.n_sensors, a.n_rays_total, a.n_tris, fl & 0x27u)] = best;
     if (out_ms) *out_ms = best_ms;
     // leave the outputs holding a valid frame from the chosen configuration
     CastArgs b = a;

@@ -48,7 +48,11 @@ struct SensorDev {
     float lut_lo;         // channel lookup table: bin b covers sin(elevation) from lut_lo + b / lut_inv_w
     float lut_inv_w;
     uint32_t lut_off;     // offset of this sensor's table in the global lookup-table array
-    uint32_t pad_;
+    float az_noise_pad;   // widening of ray spans (ray units) for per-ray azimuth perturbations
+    const uint32_t* mask; // on/off bits over the channel x ray grid (nullptr: every ray fires)
+    unsigned long long noise_seed;
+    float range_sigma;    // post-hoc range noise (0: off)
+    uint32_t pad2_;
 };
 
 // Channel lookup table: LUT_BINS bins over [sin(elev_0) - 0.01, sin(elev_last) + 0.01];
@@ -140,6 +144,8 @@ struct CastArgs {
     uint32_t* out_tri;
     unsigned long long* surv;  // (triangle, sensor, channel span) pairs that pass the elevation cull
     uint32_t surv_cap;
+    float area_eps2;           // eps_A^2 of the lossy apparent-area cull (flag bit 5)
+    uint32_t post;             // 1: some sensor of the cast has a ray mask or range noise
 };
 
 struct LaunchCfg {

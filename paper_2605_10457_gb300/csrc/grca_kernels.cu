@@ -723,7 +723,8 @@ __device__ __forceinline__ uint32_t pack_span(int jl, int jh, bool pierced) {
 // the channel span from the elevation range.  Returns false when culled.
 template <bool RECHECK, bool BRUTE, typename T>
 __device__ __forceinline__ bool cull_elevation(const SensorDev& S, const T* ch, const uint16_t* lut, const V3 v[3],
-                                               const V3& nw, const float eeT[3], bool cull_back, uint32_t& span) {
+                                               const V3& nw, const float eeT[3], bool cull_back, bool lossy_area,
+                                               float area_eps2, uint32_t& span) {
     V3 w0 = rel_origin(S, v[0]);
     if (cull_back) {
         float det = vdot(w0, nw);
@@ -739,6 +740,14 @@ __device__ __forceinline__ bool cull_elevation(const SensorDev& S, const T* ch, 
         return true;
     }
     const V3 wv[3] = {w0, rel_origin(S, v[1]), rel_origin(S, v[2])};
+    if (lossy_area) {
+        // Eq. apparent_area: A_T (c-o).n^ = (c-o).n / 2 with n = (v1-v0)x(v2-v0)
+        V3 wc = {(wv[0].x + wv[1].x + wv[2].x) * (1.f / 3.f), (wv[0].y + wv[1].y + wv[2].y) * (1.f / 3.f),
+                 (wv[0].z + wv[1].z + wv[2].z) * (1.f / 3.f)};
+        float dc = 0.5f * (wc.x * nw.x + wc.y * nw.y + wc.z * nw.z);
+        float r2c = wc.x * wc.x + wc.y * wc.y + wc.z * wc.z;
+        if (dc * dc < area_eps2 * r2c * r2c * r2c) return false;
+    }
     float smin, smax;
     bool pierced = elev_range_w(S, wv, eeT, smin, smax);
     int jl = chan_lower(S, ch, lut, smin - EPS_S);
@@ -795,7 +804,7 @@ __device__ __forceinline__ void cull_rest(const CastArgs& a, const SensorDev& S,
                 B = sp.a0 + hi * S.inv_dtheta;
             }
         }
-        if (!ray_interval(S, A - PADR, B + PADR, sp.u_lo, sp.n_r)) return;
+        if (!ray_interval(S, A - PADR - S.az_noise_pad, B + PADR + S.az_noise_pad, sp.u_lo, sp.n_r)) return;
     }
     const uint32_t ncand = (uint32_t)(sp.j_hi - sp.j_lo + 1) * (uint32_t)sp.n_r;
     c.live++;
@@ -932,7 +941,8 @@ __global__ void __launch_bounds__(256, 3) k_cull(CastArgs a) {
                 for (uint32_t k = 0; k < ng; ++k) {
                     uint32_t span;
                     if (cull_elevation<RECHECK, BRUTE>(M.sens[sg + k], M.ch + M.sens[sg + k].ch_loc,
-                                                       M.lut + (sg + k) * LUT_BINS, v, nw, eeT, cull_back, span)) {
+                                                       M.lut + (sg + k) * LUT_BINS, v, nw, eeT, cull_back,
+                                                       (a.flags & 32u) != 0, a.area_eps2, span)) {
                         mask |= 1u << k;
                         W.span[lane * CULL_GROUP + k] = span;
                     }
@@ -1072,6 +1082,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     CullAWarpSmem& W = reinterpret_cast<CullAWarpSmem*>(M.rest)[wib];
     const bool cull_back = a.flags & 2u;
+    const bool lossy_area = a.flags & 32u;
     uint32_t fill = 0;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t gwarp = ((blockIdx.x * blockDim.x) >> 5) + wib;
@@ -1096,7 +1107,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
                 uint32_t span = 0;
                 const SensorDev& S = M.sens[sg + k];
                 bool ok = valid && cull_elevation<RECHECK, BRUTE>(S, M.sins + S.ch_loc, M.lut + (sg + k) * LUT_BINS, v,
-                                                                  nw, eeT, cull_back, span);
+                                                                  nw, eeT, cull_back, lossy_area, a.area_eps2, span);
                 uint32_t bal = __ballot_sync(0xffffffffu, ok);
                 if (ok)
                     W.buf[fill + __popc(bal & ((1u << lane) - 1u))] =
@@ -1191,7 +1202,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
                             B = sp.a0 + hi * S.inv_dtheta;
                         }
                     }
-                    keep = ray_interval(S, A - PADR, B + PADR, sp.u_lo, sp.n_r);
+                    keep = ray_interval(S, A - PADR - S.az_noise_pad, B + PADR + S.az_noise_pad, sp.u_lo, sp.n_r);
                 }
             }
             if (keep) {
@@ -1455,7 +1466,8 @@ __global__ void __launch_bounds__(256) k_expand(CastArgs a) {
                     if (channel_span_rel(p, s_v, sc.x, sc.y, lo, hi)) {
                         int ru, rn;
                         if (hi - lo < 6.2831f &&
-                            ray_interval(S, P.a0 + lo * S.inv_dtheta - PADR, P.a0 + hi * S.inv_dtheta + PADR, ru, rn)) {
+                            ray_interval(S, P.a0 + lo * S.inv_dtheta - PADR - S.az_noise_pad,
+                                         P.a0 + hi * S.inv_dtheta + PADR + S.az_noise_pad, ru, rn)) {
                             if (full_pair) {
                                 u_lo = ru;
                                 n_r = rn;
@@ -1654,14 +1666,47 @@ __global__ void k_recheck_pairs(CastArgs a) {
     if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&a.counters[C_RECHECK], (unsigned long long)kept);
 }
 
+// output function of SplitMix64 (Steele, Lea and Flood, 2014) for state x
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Post-processing of one ray (App. A.3 masks, App. A.1 range noise): a ray
+// that does not fire reports a miss; a hit gets sigma * z added, z a
+// Box-Muller normal from two counter-based uniforms of the ray's index.
+__device__ __forceinline__ void post_ray(const CastArgs& a, uint32_t g, float& dist, uint32_t& id) {
+    uint32_t sn = 0;
+    for (uint32_t k = 1; k < a.n_sensors; ++k)
+        if (a.sensors[k].ray_off <= g) sn = k;
+    const SensorDev& S = a.sensors[sn];
+    const uint32_t q = g - S.ray_off;
+    if (S.mask && !((S.mask[q >> 5] >> (q & 31u)) & 1u)) {
+        dist = __uint_as_float(0x7F800000u);
+        id = NO_HIT;
+        return;
+    }
+    if (S.range_sigma > 0.f && id != NO_HIT) {
+        const unsigned long long c = S.noise_seed + 2ull * q;
+        const float u1 = (float)((splitmix64(c) >> 40) + 1ull) * 5.9604645e-08f;  // (0, 1]
+        const float u2 = (float)(splitmix64(c + 1ull) >> 40) * 5.9604645e-08f;    // [0, 1)
+        dist += S.range_sigma * (sqrtf(-2.f * logf(u1)) * cospif(2.f * u2));
+    }
+}
+
 // R3 fused into decode: flagged rays take the FP64 key
 __global__ void k_decode(CastArgs a, int recheck) {
     uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_rays_total; g += stride) {
         unsigned long long k = a.keys[g];
         if (recheck && (a.flag_bits[g >> 5] >> (g & 31u) & 1u)) k = a.keys64[g];
-        a.out_dist[g] = __uint_as_float((uint32_t)(k >> 32));
-        a.out_tri[g] = (uint32_t)k;
+        float dist = __uint_as_float((uint32_t)(k >> 32));
+        uint32_t id = (uint32_t)k;
+        if (a.post) post_ray(a, g, dist, id);
+        a.out_dist[g] = dist;
+        a.out_tri[g] = id;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_PAIRS] = (unsigned long long)a.n_tris * a.n_sensors;
 }

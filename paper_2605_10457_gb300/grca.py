@@ -22,6 +22,7 @@ CAST_CULL_BACKFACE = 1 << 1
 CAST_BRUTE = 1 << 2
 CAST_GRAPH = 1 << 3
 CAST_DUMP_CANDIDATES = 1 << 4
+CAST_LOSSY_AREA = 1 << 5
 NO_HIT = 0xFFFFFFFF
 
 
@@ -29,7 +30,8 @@ class grca_options(ctypes.Structure):
     _fields_ = [("big_pair_capacity", ctypes.c_uint64), ("chunk_capacity", ctypes.c_uint64),
                 ("recheck_capacity", ctypes.c_uint64), ("inline_max", ctypes.c_uint32),
                 ("chunk_rays", ctypes.c_uint32), ("cull_block", ctypes.c_uint32),
-                ("cull_blocks_per_sm", ctypes.c_uint32), ("survivor_capacity", ctypes.c_uint64)]
+                ("cull_blocks_per_sm", ctypes.c_uint32), ("survivor_capacity", ctypes.c_uint64),
+                ("area_eps", ctypes.c_double)]
 
 
 class grca_sensor_desc(ctypes.Structure):
@@ -60,7 +62,8 @@ _LIB = None
 EXPORTS = ["grca_create", "grca_destroy", "grca_create_sensor", "grca_set_sensor_pose", "grca_upload_triangles",
            "grca_update_vertices", "grca_cast", "grca_cast_host", "grca_autotune", "grca_set_debug_dump",
            "grca_get_stats", "grca_last_launch_count", "grca_profile_enable", "grca_profile_read",
-           "grca_status_string", "grca_last_cuda_error", "grca_cast_noalloc"]
+           "grca_status_string", "grca_last_cuda_error", "grca_cast_noalloc",
+           "grca_set_ray_mask", "grca_set_sensor_azimuths", "grca_set_range_noise"]
 
 
 def library_path() -> str:
@@ -107,6 +110,12 @@ def _lib_handle(build_if_missing: bool = True):
     lib.grca_profile_read.argtypes = [P, u32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_uint64),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32)]
     lib.grca_profile_read.restype = i32
+    lib.grca_set_ray_mask.argtypes = [P, i32, P, ctypes.c_int, P]
+    lib.grca_set_ray_mask.restype = i32
+    lib.grca_set_sensor_azimuths.argtypes = [P, i32, P]
+    lib.grca_set_sensor_azimuths.restype = i32
+    lib.grca_set_range_noise.argtypes = [P, i32, ctypes.c_double, ctypes.c_uint64]
+    lib.grca_set_range_noise.restype = i32
     lib.grca_cast_noalloc.argtypes = [ctypes.POINTER(grca_sensor_desc), P, u32, P, P, u32, P]
     lib.grca_cast_noalloc.restype = i32
     lib.grca_status_string.argtypes = [i32]
@@ -157,7 +166,7 @@ class Caster:
         self.device = device
         o = grca_options()
         for k, v in opts.items():
-            setattr(o, k, int(v))
+            setattr(o, k, float(v) if k == "area_eps" else int(v))
         ctx = ctypes.c_void_p()
         torch.cuda.set_device(device)
         st = self.lib.grca_create(ctypes.byref(ctx), device, ctypes.byref(o))
@@ -207,7 +216,40 @@ class Caster:
         self._check(self.lib.grca_create_sensor(self.ctx, ctypes.byref(d), ctypes.byref(sid)), "grca_create_sensor")
         self.sensors.append(s)
         self._elev.append(elev)
+        az = getattr(s, "azimuths", None)
+        if az is not None:
+            self.set_azimuths(sid.value, az)
         return sid.value
+
+    def set_azimuths(self, sid: int, theta=None):
+        """Per-ray azimuths (radians) replacing the uniform grid; None restores it."""
+        if theta is None:
+            self._check(self.lib.grca_set_sensor_azimuths(self.ctx, sid, None), "grca_set_sensor_azimuths")
+            return
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        self._check(self.lib.grca_set_sensor_azimuths(self.ctx, sid, th.ctypes.data), "grca_set_sensor_azimuths")
+
+    def set_ray_mask(self, sid: int, bits=None, stream=None):
+        """On/off bits over the sensor's channel x ray grid (uint32 words; bit q & 31 of
+        word q >> 5 for ray q = j*n_rays + i).  numpy: host copy; CUDA tensor: device copy."""
+        torch = self.torch
+        if bits is None:
+            st = self.lib.grca_set_ray_mask(self.ctx, sid, None, GRCA_MEM_HOST, _stream_ptr(stream))
+        elif isinstance(bits, torch.Tensor) and bits.is_cuda:
+            b = bits.contiguous()
+            st = self.lib.grca_set_ray_mask(self.ctx, sid, b.data_ptr(), GRCA_MEM_DEVICE, _stream_ptr(stream))
+        else:
+            b = np.ascontiguousarray(bits, dtype=np.uint32)
+            s = self.sensors[sid]
+            if b.size * 32 < len(s.elev) * int(s.n_rays):
+                raise ValueError("ray mask shorter than the sensor's channel x ray grid")
+            st = self.lib.grca_set_ray_mask(self.ctx, sid, b.ctypes.data, GRCA_MEM_HOST, _stream_ptr(stream))
+        self._check(st, "grca_set_ray_mask")
+
+    def set_range_noise(self, sid: int, sigma: float, seed: int = 0):
+        """Post-hoc range noise sigma * N(0, 1) on every hit distance of the sensor."""
+        self._check(self.lib.grca_set_range_noise(self.ctx, sid, float(sigma), int(seed) & (2**64 - 1)),
+                    "grca_set_range_noise")
 
     def set_pose(self, sid: int, origin, f, r, u):
         arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (origin, f, r, u)]
@@ -325,5 +367,5 @@ class Caster:
 
 
 __all__ = ["Caster", "GrcaError", "CAST_FP64_RECHECK", "CAST_CULL_BACKFACE", "CAST_BRUTE", "CAST_GRAPH",
-           "CAST_DUMP_CANDIDATES", "NO_HIT", "EXPORTS", "library_path", "grca_options", "grca_sensor_desc",
+           "CAST_DUMP_CANDIDATES", "CAST_LOSSY_AREA", "NO_HIT", "EXPORTS", "library_path", "grca_options", "grca_sensor_desc",
            "grca_stats"]

@@ -34,7 +34,8 @@ DT = 0.01  # frame step, seconds (the paper's 100 Hz simulation clock)
 class Sensor:
     """One spinning LiDAR: origin, orthonormal axes (forward f, right r, up u),
     ascending channel elevations (radians), a uniform azimuth grid
-    theta_i = theta0 + i*dtheta for i in [0, n_rays), and the range [d_min, d_max]."""
+    theta_i = theta0 + i*dtheta for i in [0, n_rays) (or, with noise, the
+    listed per-ray azimuths), and the range [d_min, d_max]."""
     origin: np.ndarray
     f: np.ndarray
     r: np.ndarray
@@ -45,6 +46,7 @@ class Sensor:
     dtheta: float
     d_min: float = 0.0
     d_max: float = math.inf
+    azimuths: Optional[np.ndarray] = None   # per-ray azimuths replacing the uniform grid (noise)
 
     @property
     def n_channels(self) -> int:
@@ -107,6 +109,42 @@ def make_sensor(origin, yaw: float = 0.0, channels: str = "t128", n_rays: int = 
     return Sensor(origin=np.asarray(origin, dtype=np.float64), f=f, r=r, u=u,
                   elev=np.asarray(elev, dtype=np.float64), n_rays=int(n_rays),
                   theta0=float(theta0), dtheta=float(dtheta), d_min=float(d_min), d_max=float(d_max))
+
+
+def noisy_sensor(s: Sensor, seed: int, az_frac: float = 0.45, elev_frac: float = 0.3) -> Sensor:
+    """Copy of `s` with per-ray azimuths drawn uniformly within +-az_frac*dtheta of the
+    grid and channel elevations moved by up to +-elev_frac of the smaller neighbouring
+    gap (so they stay ascending): horizontal and vertical angular noise."""
+    rng = np.random.default_rng(seed)
+    th = s.theta0 + np.arange(s.n_rays) * s.dtheta + rng.uniform(-az_frac, az_frac, s.n_rays) * s.dtheta
+    e = np.asarray(s.elev, np.float64)
+    gap = np.diff(e)
+    lim = np.minimum(np.concatenate([[gap[0]], gap]), np.concatenate([gap, [gap[-1]]])) if e.size > 1 else \
+        np.array([1e-3])
+    e2 = e + rng.uniform(-elev_frac, elev_frac, e.size) * lim
+    return dataclasses.replace(s, elev=e2, azimuths=th)
+
+
+def ray_mask(s: Sensor, seed: int, density: float = 0.5, kind: str = "random") -> np.ndarray:
+    """uint32 on/off words over the channel x ray grid (bit q & 31 of word q >> 5 for
+    q = j*n_rays + i): "random" (each ray fires with probability `density`),
+    "sector" (a contiguous azimuth window of a non-spinning sensor) or "stripes"
+    (every other channel, a scan-pattern image)."""
+    n = s.n_channels * s.n_rays
+    j, i = np.divmod(np.arange(n), s.n_rays)
+    if kind == "random":
+        on = np.random.default_rng(seed).random(n) < density
+    elif kind == "sector":
+        w = max(1, int(density * s.n_rays))
+        start = int(np.random.default_rng(seed).integers(s.n_rays))
+        on = ((i - start) % s.n_rays) < w
+    elif kind == "stripes":
+        on = (j + seed) % 2 == 0
+    else:
+        raise ValueError(kind)
+    bits = np.zeros(((n + 31) // 32) * 32, bool)
+    bits[:n] = on
+    return np.packbits(bits.reshape(-1, 32)[:, ::-1], axis=1).view(">u4").astype(np.uint32).ravel()
 
 
 def ray_offsets(sensors: List[Sensor]) -> np.ndarray:

@@ -61,6 +61,7 @@ def grade(orc: "oracle.Oracle", tris: np.ndarray, ref: dict, gpu_t: np.ndarray, 
         res["hit_miss"] += 1
         res["bad_rays"].append(("hitmiss", int(ray_ids[k]), float(ot[k]), float(gt[k]), int(oid[k]), int(gid[k]),
                                 float(m)))
+    res["bad_ids"] = [b[1] for b in res["bad_rays"]]
     res["bad_rays"] = res["bad_rays"][:20]
     res["errors"] = res["id_mismatch"] + res["hit_miss"] + res["dist_bad"]
     return res

@@ -14,7 +14,7 @@ import os
 import numpy as np
 
 import oracle
-from scenes import make_sensor, scene_c1, Sensor
+from scenes import make_sensor, ray_mask, scene_c1, Sensor
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
@@ -260,6 +260,125 @@ def check_triangle_hits(lib=None):
     assert got == expect and len(got) > 10
 
 
+def check_area_keep(lib=None):
+    """Eq. apparent_area: a triangle facing the sensor at distance r with area A
+    has apparent area A / r^2 (cos = 1); kept iff A / r^2 >= eps.  Edge-on: dropped."""
+    s = _sensor(h=0.0, n_rays=8, elev_deg=(0,))
+    eps = 1e-6
+    o = oracle.Oracle([s], lib)
+    rows = []
+    for A, r in ((1e-4, 5.0), (1e-4, 20.0), (1e-2, 50.0), (1e-2, 150.0), (4.0, 1000.0), (4.0, 3000.0)):
+        L = math.sqrt(2.0 * A)   # right triangle with legs L: area L^2 / 2
+        c = np.array([r, 0.0, 0.0])
+        tri = np.array([c + [0, -L / 3, -L / 3], c + [0, 2 * L / 3, -L / 3], c + [0, -L / 3, 2 * L / 3]])
+        rows.append((A / r ** 2 >= eps, tri))
+    edge_on = np.array([[5.0, 0.0, -0.5], [6.0, 0.0, -0.5], [5.5, 0.0, 0.5]])   # plane y = 0 contains o
+    tris = np.array([t for _, t in rows] + [edge_on], np.float32)
+    keep = oracle.area_keep(o, tris, eps)[0]
+    for k, (expect, _) in enumerate(rows):
+        assert bool(keep[k]) == expect, (k, keep[k], expect)
+    assert keep[-1] == 0
+    # the keep mask hides dropped triangles from the cast
+    r = oracle.cast(o, tris[:1], keep=np.zeros((1, 1), np.uint8))
+    assert np.all(r["id"] == oracle.NO_HIT)
+
+
+def check_splitmix64(lib=None):
+    """SplitMix64's published output sequence for state 0: output n is sm(n * gamma)."""
+    g = json.load(open(os.path.join(GOLDEN, "splitmix64.json")))
+    gamma = 0x9E3779B97F4A7C15
+    for n, h in enumerate(g["outputs_hex"]):
+        assert oracle.splitmix64((g["seed_state"] + n * gamma) % 2**64, lib=lib) == int(h, 16), n
+
+
+def _normal_cdf(x):
+    return 0.5 * (1.0 + np.vectorize(math.erf)(x / math.sqrt(2.0)))
+
+
+def check_range_noise(lib=None):
+    """Range noise z must be standard normal (Box-Muller) and uncorrelated across
+    neighbouring rays and seeds: moments, a Kolmogorov-Smirnov distance and lag-1
+    correlation, at bounds 5+ standard errors wide for n = 200k draws."""
+    n = 200_000
+    q = np.arange(n, dtype=np.int64)
+    z = oracle.range_noise(12345, q, lib=lib)
+    assert np.all(np.isfinite(z))
+    assert abs(z.mean()) < 5.0 / math.sqrt(n)
+    assert abs(z.var() - 1.0) < 5.0 * math.sqrt(2.0 / n)
+    zs = np.sort(z)
+    ks = np.max(np.abs(_normal_cdf(zs) - (np.arange(n) + 0.5) / n))
+    assert ks < 1.63 / math.sqrt(n) + 1.0 / n      # 1% critical value of the KS statistic
+    assert abs(np.corrcoef(z[:-1], z[1:])[0, 1]) < 5.0 / math.sqrt(n)
+    z2 = oracle.range_noise(12346, q, lib=lib)
+    assert abs(np.corrcoef(z, z2)[0, 1]) < 5.0 / math.sqrt(n)
+    # deterministic in (seed, q): the same draws for a shuffled query
+    perm = np.random.default_rng(0).permutation(n)[:1000]
+    assert np.array_equal(oracle.range_noise(12345, q[perm], lib=lib), z[perm])
+
+
+def check_azimuth_list(lib=None):
+    """Per-ray azimuths (horizontal noise): a list equal to a grid shifted by c
+    gives exactly the results of the uniform sensor with theta0 + c, and a
+    permuted-free random list hits the triangles predicted by an independent
+    linear solve along each listed direction."""
+    rng = np.random.default_rng(11)
+    tris = rng.normal(0, 4, (60, 3, 3)).astype(np.float32)
+    tris[:, :, 2] = np.abs(tris[:, :, 2])
+    base = _sensor(h=1.0, n_rays=96)
+    c = 0.5 * base.dtheta
+    shifted = Sensor(**{**base.__dict__, "theta0": base.theta0 + c})
+    listed = Sensor(**{**base.__dict__, "azimuths": base.theta0 + c + np.arange(base.n_rays) * base.dtheta})
+    r_s = oracle.cast(oracle.Oracle([shifted], lib), tris)
+    r_l = oracle.cast(oracle.Oracle([listed], lib), tris)
+    r_b = oracle.cast(oracle.Oracle([base], lib), tris)
+    assert np.array_equal(r_s["id"], r_l["id"])
+    hit = r_s["id"] != oracle.NO_HIT
+    assert np.allclose(r_s["t"][hit], r_l["t"][hit], rtol=1e-12)
+    assert np.count_nonzero(r_b["id"] != r_s["id"]) > 5       # the shift matters on this scene
+    # each listed azimuth is used for its own ray: check a random list ray by ray
+    th = base.theta0 + np.arange(base.n_rays) * base.dtheta + rng.uniform(-0.45, 0.45, base.n_rays) * base.dtheta
+    noisy = Sensor(**{**base.__dict__, "azimuths": th})
+    r_n = oracle.cast(oracle.Oracle([noisy], lib), tris)
+    f, rr, u = base.f, base.r, base.u
+    for q in range(0, noisy.n_total, 7):
+        j, i = divmod(q, noisy.n_rays)
+        ph = base.elev[j]
+        d = math.cos(ph) * (math.cos(th[i]) * f + math.sin(th[i]) * rr) + math.sin(ph) * u
+        best, bid = math.inf, oracle.NO_HIT
+        for k in range(tris.shape[0]):
+            v = tris[k].astype(np.float64)
+            M = np.stack([v[1] - v[0], v[2] - v[0], -d], 1)
+            if abs(np.linalg.det(M)) < 1e-12:
+                continue
+            a, b, t = np.linalg.solve(M, base.origin - v[0])
+            if min(a, b, 1 - a - b) > 1e-9 and t > 0 and t < best:
+                best, bid = t, k
+        assert r_n["id"][q] == bid, (q, r_n["id"][q], bid)
+
+
+def check_ray_mask(lib=None):
+    """A ray that does not fire is a miss; the others are unchanged.  Bit order:
+    bit q & 31 of word q >> 5 for q = j*n_rays + i (a single set bit fires exactly
+    that ray)."""
+    s = _sensor(h=1.8, n_rays=40)
+    tris = _quad(-50, 50, -50, 50, 0.0)
+    full = oracle.cast(oracle.Oracle([s], lib), tris)
+    hits = np.nonzero(full["id"] != oracle.NO_HIT)[0]
+    assert hits.size > 40
+    for q in (int(hits[0]), int(hits[len(hits) // 2]), int(hits[-1])):
+        m = np.zeros((s.n_total + 31) // 32, np.uint32)
+        m[q >> 5] = np.uint32(1) << np.uint32(q & 31)
+        r = oracle.cast(oracle.Oracle([s], lib, masks=[m]), tris)
+        assert np.nonzero(r["id"] != oracle.NO_HIT)[0].tolist() == [q]
+        assert r["t"][q] == full["t"][q]
+    m = ray_mask(s, 4, 0.5)
+    r = oracle.cast(oracle.Oracle([s], lib, masks=[m]), tris)
+    on = np.array([(int(m[q >> 5]) >> (q & 31)) & 1 for q in range(s.n_total)], bool)
+    assert np.array_equal(r["id"][on], full["id"][on]) and np.all(r["id"][~on] == oracle.NO_HIT)
+    assert np.all(np.isinf(r["t"][~on]))
+
+
 ALL_CHECKS = [check_brute_count, check_ray_grid, check_ground, check_wall, check_straddle, check_front,
               check_coplanar_tie, check_fan, check_backface, check_range, check_linear_solve, check_margin,
-              check_triangle_hits]
+              check_triangle_hits, check_area_keep, check_splitmix64, check_range_noise, check_azimuth_list,
+              check_ray_mask]

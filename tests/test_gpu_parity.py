@@ -154,6 +154,41 @@ def test_range_cull_c4m(d_max):
     assert g["errors"] == 0, g
 
 
+def test_lossy_apparent_area_mode():
+    """GRCA_CAST_LOSSY_AREA (App. A.4.1 Step 1, Eq. apparent_area): the result
+    equals the oracle over the triangles the FP64 filter keeps, except on rays
+    whose outcome involves a triangle within 1e-3 of the threshold (there FP32
+    and FP64 may decide differently).  Also reports the paper's Hit% floor
+    against the exact result (distance within 1 mm)."""
+    from paper_2605_10457_gb300.grca import CAST_FP64_RECHECK, CAST_LOSSY_AREA
+    eps = 1e-5
+    sc = make_config("c4m")
+    c, ids, tris = _setup(sc, frame=1, area_eps=eps)
+    d, t = _cast(c, ids, CAST_FP64_RECHECK | CAST_LOSSY_AREA)
+    st = c.stats()
+    d_exact, t_exact = _cast(c, ids, CAST_FP64_RECHECK)
+    st_exact = c.stats()
+    assert st["pairs_live"] < st_exact["pairs_live"]
+    keep = oracle.area_keep(sc.sensors, tris, eps)
+    rays = stratified_rays(sc.sensors, 400, seed=11)
+    orc = oracle.Oracle(sc.sensors)
+    bad = None
+    for kmask in ((keep > 0), (keep == 1)):
+        ref = oracle.cast(orc, tris, rays, ties=True, keep=kmask.astype(np.uint8))
+        g = grade(orc, tris, ref, d[rays], t[rays])
+        bad = set(g["bad_ids"]) if bad is None else bad & set(g["bad_ids"])
+    assert not bad, sorted(bad)[:10]
+    # Hit% (paper: hit distance within 1 mm of the exact one, or both miss)
+    m_exact = np.isfinite(d_exact[rays])
+    m_lossy = np.isfinite(d[rays])
+    close = np.zeros(rays.shape[0], bool)
+    both = m_exact & m_lossy
+    close[both] = np.abs(d[rays][both] - d_exact[rays][both]) <= 1e-3
+    same = (~m_exact & ~m_lossy) | close
+    print(f"lossy eps={eps}: Hit% = {100 * same.mean():.2f}, live pairs {st['pairs_live']} vs {st_exact['pairs_live']}")
+    assert same.mean() > 0.5
+
+
 def test_backface_cull_c1():
     from paper_2605_10457_gb300.grca import CAST_CULL_BACKFACE, CAST_FP64_RECHECK
     sc = scene_c1()

@@ -38,6 +38,15 @@ MUTANTS = [
     ("channel index taken from the ray index", "double ph = s->elev[j];", "double ph = s->elev[i % s->n_channels];"),
     ("behind-origin hits accepted", "if (!(t > 0.0)) return 0;", "if (t == 0.0) return 0;"),
     ("transposed cross product operands", "cross3(ab, ax, c);", "cross3(ax, ab, c);"),
+    ("apparent-area threshold not squared", "double rhs = eps * eps * r2 * r2 * r2;", "double rhs = eps * r2 * r2 * r2;"),
+    ("Box-Muller radius without the factor 2", "z[k] = sqrt(-2.0 * log(u1))", "z[k] = sqrt(-log(u1))"),
+    ("SplitMix64 second shift wrong", "z = (z ^ (z >> 27))", "z = (z ^ (z >> 28))"),
+    ("both uniforms from the same counter", "double u2 = (double)(orc_splitmix64(c + 1ull) >> 40)",
+     "double u2 = (double)(orc_splitmix64(c) >> 40)"),
+    ("listed azimuth taken from the channel index", "double th = s->theta ? s->theta[i]",
+     "double th = s->theta ? s->theta[j % s->n_rays]"),
+    ("ray mask bit order reversed", "if (s->mask && !((s->mask[q >> 5] >> (q & 31u)) & 1u)) {",
+     "if (s->mask && !((s->mask[q >> 5] >> (31u - (q & 31u))) & 1u)) {"),
 ]
 
 
