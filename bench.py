@@ -135,6 +135,9 @@ def run_reference(args):
         return 0
     from scenes import make_config
     sc = make_config(args.config)
+    if args.d_max is not None:
+        for s_ in sc.sensors:
+            s_.d_min, s_.d_max = 0.05, float(args.d_max)
     tris = sc.tris(0)
     import oracle
     sys.path.insert(0, os.path.join(ROOT, "tests"))
@@ -184,6 +187,11 @@ def main():
     ap.add_argument("--capacity", default="large", choices=["large", "small"],
                     help="device work-queue capacities (small: ~2 GB, for profiler captures)")
     ap.add_argument("--lean", action="store_true", help="headline leg only (no plain / profile / e2e legs)")
+    ap.add_argument("--no-group-cull", action="store_true", help="A/B: turn off the group-level (GACP-T_g) cull")
+    ap.add_argument("--hybrid", action="store_true",
+                    help="hybrid static/dynamic pipeline: static triangles through a hierarchy built once")
+    ap.add_argument("--d-max", type=float, default=None,
+                    help="range variant: every sensor gets [0.05 m, d_max] (default: the workload's own range)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -201,6 +209,9 @@ def main():
     from scenes import make_config
 
     sc = make_config(args.config)
+    if args.d_max is not None:
+        for s_ in sc.sensors:
+            s_.d_min, s_.d_max = 0.05, float(args.d_max)
     ns, nd = sc.n_static, sc.n_dynamic
     frames_host = [sc.dynamic_tris(f % sc.n_frames) for f in range(args.frames)]
     full0 = np.ascontiguousarray(np.concatenate([sc.static_tris, frames_host[0]], 0))
@@ -213,10 +224,16 @@ def main():
     c = grca.Caster(local, **caps)
     ids = [c.add_sensor(s) for s in sc.sensors]
     c.upload(full0)
+    build_s = None
+    if args.hybrid and ns:
+        # hybrid static/dynamic pipeline: static hierarchy built once, outside the timed region
+        t_b = time.time()
+        c.build_static(ns)
+        build_s = time.time() - t_b
     n_rays = sc.n_rays
     out = c.outputs(ids)
     stream = torch.cuda.current_stream()
-    FL = grca.CAST_FP64_RECHECK
+    FL = grca.CAST_FP64_RECHECK | (grca.CAST_NO_GROUP_CULL if args.no_group_cull else 0)
 
     tune_ms = None
     if not args.no_autotune:
@@ -235,7 +252,7 @@ def main():
         f = (rank + k * ws) % args.frames
         c.update(frames_dev[f], ns)
         for i, sid in enumerate(ids):
-            c.cast([sid], grca.CAST_GRAPH, plain_out[i])
+            c.cast([sid], grca.CAST_GRAPH | (FL & grca.CAST_NO_GROUP_CULL), plain_out[i])
 
     def barrier():
         torch.cuda.synchronize()
@@ -244,16 +261,21 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(fn, steps, warmup):
+    def timed(fn, steps, warmup, profiler_range=False):
         for k in range(warmup):
             fn(k)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        if profiler_range:
+            # lets `ncu --profile-from-start off` capture exactly the timed steps
+            torch.cuda.profiler.start()
         e0.record(stream)
         for k in range(steps):
             fn(warmup + k)
         e1.record(stream)
+        if profiler_range:
+            torch.cuda.profiler.stop()
         barrier()
         ms = e0.elapsed_time(e1)
         if ws > 1:
@@ -265,7 +287,7 @@ def main():
 
     # --- headline: batched FP32 + FP64 recheck, CUDA-graph replay -------------
     clk = Clocks(local)
-    ms_b = timed(step_batched, args.steps, args.warmup)
+    ms_b = timed(step_batched, args.steps, args.warmup, profiler_range=True)
     clocks = clk.stop()
     launches_per_frame = c.last_launch_count()
     st = c.stats(check=False)
@@ -360,7 +382,10 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{args.config}: {len(sc.sensors)} LiDARs x {sc.sensors[0].n_channels}x"
                                f"{sc.sensors[0].n_rays} 360deg, {sc.n_tris} tris ({nd} dynamic), batched "
-                               f"FP32+FP64-recheck, CUDA-graph replay",
+                               f"FP32+FP64-recheck, CUDA-graph replay"
+                               + (f", range [0.05, {args.d_max:g}] m" if args.d_max is not None else "")
+                               + (f", hybrid: {ns} static tris through a hierarchy built once" if build_s is not None
+                                  else ""),
                    "rays_per_frame": n_rays, "triangles": sc.n_tris, "dynamic_triangles": nd,
                    "sensors": len(sc.sensors), "frames_cycled": args.frames,
                    "l2": "inputs larger than L2 (vertex stream 0.78 GB per frame)",
@@ -379,6 +404,7 @@ def main():
                                           "chunks", "tests", "hits", "uncertain", "ties", "flagged_rays",
                                           "recheck_pairs")},
         "autotune_ms": tune_ms,
+        "static_build_s": build_s,
         "device_error": st_prof["device_error"],
     }
     if rank == 0:

@@ -76,7 +76,16 @@ enum {
      * A_T the area, c the centroid and n^ the unit normal; eps_A =
      * grca_options.area_eps (default 1e-6, the paper's value).  Drops true
      * hits on small, far or edge-on triangles by design. */
-    GRCA_CAST_LOSSY_AREA = 1u << 5
+    GRCA_CAST_LOSSY_AREA = 1u << 5,
+    /* Turn off the group-level cull (GACP-T_g, Sec. 10.1.1).  That cull is
+     * lossless and runs by default whenever some sensor of the cast has a
+     * finite d_max: each 32-triangle group's box (kept current by uploads
+     * and vertex updates) is tested against every sensor's range and channel
+     * window before any per-triangle work.  For debugging and A/B timing. */
+    GRCA_CAST_NO_GROUP_CULL = 1u << 6,
+    /* Trace the static triangles through the culls even when a static
+     * hierarchy exists (grca_build_static): for A/B timing and debugging. */
+    GRCA_CAST_NO_STATIC_BVH = 1u << 7
 };
 
 /* Context options (all fields 0 = library default). */
@@ -134,6 +143,9 @@ typedef struct {
     uint64_t ties;            /* tie events between FP32 hits on one ray */
     uint64_t flagged_rays;    /* rays resolved by the FP64 re-test */
     uint64_t recheck_pairs;   /* queued (ray, triangle) pairs kept by the filter and re-tested in FP64 */
+    uint64_t group_culled;    /* pairs skipped whole by the group-level cull (GACP-T_g) */
+    uint64_t bvh_node_visits; /* static-hierarchy nodes visited (hybrid casts) */
+    uint64_t bvh_tests;       /* ray-triangle tests on static leaves (hybrid casts) */
     uint64_t n_rays;          /* rays in the last cast */
     uint32_t device_error;    /* bit mask of device-side errors (0 = none) */
     uint32_t reserved;
@@ -191,6 +203,21 @@ grca_status grca_cast_host(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_
  * the best frame time. */
 grca_status grca_autotune(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_sensors, float* out_dist,
                           uint32_t* out_tri, uint32_t flags, void* stream, float* out_ms);
+
+/* Hybrid static/dynamic pipeline (Sec. 7): build a bounding-volume hierarchy
+ * over triangles [0, n_static) of the uploaded set (binned SAH on the host,
+ * once; blocks until done).  Casts then trace those triangles through the
+ * hierarchy, one GPU thread per ray, and the rest through the culls; both
+ * sides commit into the same closest-hit keys, so the merge is the key
+ * minimum on the GPU and the result is the same as without the hierarchy.
+ * A cast falls back to the culls for every triangle when the static
+ * triangles were uploaded or updated after the build, when a sensor's
+ * farthest scene point is more than ~1.25 scene diagonals away, or with the
+ * BRUTE, LOSSY_AREA, DUMP_CANDIDATES or NO_STATIC_BVH flags.  n_static = 0
+ * drops the hierarchy.  Returns GRCA_ERR_INVALID_ARG if n_static exceeds
+ * the uploaded count and GRCA_ERR_CAPACITY if the tree would be deeper than
+ * the traversal stack (64). */
+grca_status grca_build_static(grca_ctx* ctx, uint32_t n_static, void* stream);
 
 /* Non-spinning and patterned sensors (App. A.3, animated ray-mask images):
  * an on/off mask over the sensor's channel x ray grid.  `bits` holds
@@ -260,7 +287,9 @@ grca_status grca_set_debug_dump(grca_ctx* ctx, uint32_t* pairs, uint64_t capacit
  * Returns GRCA_ERR_CAPACITY if a work queue overflowed in that cast. */
 grca_status grca_get_stats(grca_ctx* ctx, grca_stats* out, void* stream);
 
-/* Number of kernels the last cast launched (or replayed in its graph). */
+/* Number of kernels the last cast launched (or replayed in its graph), plus
+ * the group-bound kernels that vertex uploads and updates launched since the
+ * cast before it. */
 uint32_t grca_last_launch_count(grca_ctx* ctx);
 
 /* Per-kernel timing with CUDA events (tracing aid).  While enabled, casts

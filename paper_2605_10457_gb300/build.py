@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libgrca.so")
-SOURCES = ["grca_kernels.cu", "grca_api.cu"]
+SOURCES = ["grca_kernels.cu", "grca_api.cu", "grca_bvh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -36,7 +36,7 @@ struct SensorHost {
 };
 
 struct GraphKey {
-    uint32_t n_sensors, n_rays, total_ch, flags, n_tris;
+    uint32_t n_sensors, n_rays, total_ch, flags, n_tris, tri_first;
     const void* out_dist;
     const void* out_tri;
     const void* tris;
@@ -44,10 +44,10 @@ struct GraphKey {
     const void* dump;
     int cull_block, cull_bps, inline_max, chunk_rays;
     bool operator<(const GraphKey& o) const {
-        return std::tie(n_sensors, n_rays, total_ch, flags, n_tris, out_dist, out_tri, tris, keys, dump, cull_block,
-                        cull_bps, inline_max, chunk_rays) <
-               std::tie(o.n_sensors, o.n_rays, o.total_ch, o.flags, o.n_tris, o.out_dist, o.out_tri, o.tris, o.keys,
-                        o.dump, o.cull_block, o.cull_bps, o.inline_max, o.chunk_rays);
+        return std::tie(n_sensors, n_rays, total_ch, flags, n_tris, tri_first, out_dist, out_tri, tris, keys, dump,
+                        cull_block, cull_bps, inline_max, chunk_rays) <
+               std::tie(o.n_sensors, o.n_rays, o.total_ch, o.flags, o.n_tris, o.tri_first, o.out_dist, o.out_tri, o.tris,
+                        o.keys, o.dump, o.cull_block, o.cull_bps, o.inline_max, o.chunk_rays);
     }
 };
 
@@ -73,6 +73,16 @@ struct grca_ctx {
     cudaStream_t cap_stream = nullptr;
 
     float* d_tris = nullptr;
+    float4* d_gb = nullptr;         // GACP-T_g boxes, one pair of float4 per 32-triangle group
+    // static hierarchy of the hybrid pipeline over triangles [0, n_static)
+    BvhNode* d_bvh_nodes = nullptr;
+    uint32_t* d_bvh_prim = nullptr;
+    float* d_bvh_tris = nullptr;
+    uint32_t n_static = 0;
+    bool bvh_stale = false;         // static triangles changed since the build
+    double bvh_delta = 0.0;
+    float bvh_lo[3] = {0, 0, 0}, bvh_hi[3] = {0, 0, 0};
+    uint32_t pending_launches = 0;  // group-bound kernels launched since the last cast
     uint32_t n_tris = 0;
     size_t tris_cap = 0;  // triangles
 
@@ -116,7 +126,7 @@ struct grca_ctx {
     uint64_t dump_cap = 0;
     uint32_t* dump_count = nullptr;
 
-    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::map<GraphKey, std::pair<cudaGraphExec_t, int>> graphs;  // graph, kernels it launches
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, LaunchCfg> tuned;
 
     uint64_t last_n_rays = 0;
@@ -184,7 +194,7 @@ static grca_status cuda_fail(grca_ctx* c, cudaError_t e, const char* what) {
     } while (0)
 
 static void free_graphs(grca_ctx* ctx) {
-    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second.first);
     ctx->graphs.clear();
 }
 
@@ -304,6 +314,10 @@ void grca_destroy(grca_ctx* ctx) {
     free_graphs(ctx);
     for (SensorHost& sh : ctx->sensors) cudaFree(sh.d_mask);
     cudaFree(ctx->d_tris);
+    cudaFree(ctx->d_gb);
+    cudaFree(ctx->d_bvh_nodes);
+    cudaFree(ctx->d_bvh_prim);
+    cudaFree(ctx->d_bvh_tris);
     cudaFree(ctx->d_ch);
     cudaFree(ctx->d_ch64);
     cudaFree(ctx->d_az);
@@ -391,16 +405,25 @@ grca_status grca_upload_triangles(grca_ctx* ctx, const float* xyz, uint32_t n_tr
     if (n_tris > ctx->tris_cap) {
         CK(cudaStreamSynchronize(st));
         cudaFree(ctx->d_tris);
+        cudaFree(ctx->d_gb);
         ctx->d_tris = nullptr;
+        ctx->d_gb = nullptr;
         ctx->tris_cap = 0;
         // + 4 floats of tail padding: the culling pass stages whole float4s
         CK(cudaMalloc(&ctx->d_tris, (9ull * n_tris + 16) * sizeof(float)));
         CK(cudaMemsetAsync(ctx->d_tris, 0, (9ull * n_tris + 16) * sizeof(float), st));
+        CK(cudaMalloc(&ctx->d_gb, sizeof(float4) * 2 * ((n_tris + GROUP_TRIS - 1) / GROUP_TRIS + 1)));
         ctx->tris_cap = n_tris;
         free_graphs(ctx);
     }
     ctx->n_tris = n_tris;
-    return copy_in(ctx, ctx->d_tris, xyz, 9ull * n_tris, where, st);
+    if (ctx->n_static) ctx->bvh_stale = true;  // a new triangle set: rebuild the static hierarchy to use it
+    grca_status rs = copy_in(ctx, ctx->d_tris, xyz, 9ull * n_tris, where, st);
+    if (rs != GRCA_OK) return rs;
+    launch_group_bounds(ctx->d_tris, n_tris, 0, n_tris, ctx->d_gb, ctx->n_sm, st);
+    if (n_tris) ctx->pending_launches++;
+    CK(cudaGetLastError());
+    return GRCA_OK;
 }
 
 grca_status grca_update_vertices(grca_ctx* ctx, const float* xyz, uint32_t first, uint32_t n_tris, int where,
@@ -408,7 +431,51 @@ grca_status grca_update_vertices(grca_ctx* ctx, const float* xyz, uint32_t first
     if (!ctx || (!xyz && n_tris) || (where != GRCA_MEM_HOST && where != GRCA_MEM_DEVICE)) return GRCA_ERR_INVALID_ARG;
     if ((uint64_t)first + n_tris > ctx->n_tris) return GRCA_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
-    return copy_in(ctx, ctx->d_tris + 9ull * first, xyz, 9ull * n_tris, where, (cudaStream_t)stream);
+    if (n_tris && first < ctx->n_static) ctx->bvh_stale = true;  // static triangles moved
+    grca_status rs = copy_in(ctx, ctx->d_tris + 9ull * first, xyz, 9ull * n_tris, where, (cudaStream_t)stream);
+    if (rs != GRCA_OK) return rs;
+    launch_group_bounds(ctx->d_tris, ctx->n_tris, first, n_tris, ctx->d_gb, ctx->n_sm, (cudaStream_t)stream);
+    if (n_tris) ctx->pending_launches++;
+    CK(cudaGetLastError());
+    return GRCA_OK;
+}
+
+grca_status grca_build_static(grca_ctx* ctx, uint32_t n_static, void* stream) {
+    if (!ctx || n_static > ctx->n_tris) return GRCA_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(st));
+    CK(cudaDeviceSynchronize());  // casts in flight may still read the old hierarchy
+    cudaFree(ctx->d_bvh_nodes);
+    cudaFree(ctx->d_bvh_prim);
+    cudaFree(ctx->d_bvh_tris);
+    ctx->d_bvh_nodes = nullptr;
+    ctx->d_bvh_prim = nullptr;
+    ctx->d_bvh_tris = nullptr;
+    ctx->n_static = 0;
+    ctx->bvh_stale = false;
+    free_graphs(ctx);
+    if (n_static == 0) return GRCA_OK;
+    std::vector<float> h(9ull * n_static);
+    CK(cudaMemcpy(h.data(), ctx->d_tris, sizeof(float) * h.size(), cudaMemcpyDeviceToHost));
+    BvhHost bvh;
+    if (!build_bvh(h.data(), n_static, bvh)) return GRCA_ERR_CAPACITY;  // tree deeper than the traversal stack
+    std::vector<float> leaf(9ull * n_static);
+    for (uint32_t k = 0; k < n_static; ++k)
+        std::memcpy(&leaf[9ull * k], &h[9ull * bvh.prim[k]], 9 * sizeof(float));
+    CK(cudaMalloc(&ctx->d_bvh_nodes, sizeof(BvhNode) * bvh.nodes.size()));
+    CK(cudaMalloc(&ctx->d_bvh_prim, sizeof(uint32_t) * n_static));
+    CK(cudaMalloc(&ctx->d_bvh_tris, sizeof(float) * leaf.size()));
+    CK(cudaMemcpy(ctx->d_bvh_nodes, bvh.nodes.data(), sizeof(BvhNode) * bvh.nodes.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_bvh_prim, bvh.prim.data(), sizeof(uint32_t) * n_static, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_bvh_tris, leaf.data(), sizeof(float) * leaf.size(), cudaMemcpyHostToDevice));
+    for (int c = 0; c < 3; ++c) {
+        ctx->bvh_lo[c] = bvh.scene_lo[c];
+        ctx->bvh_hi[c] = bvh.scene_hi[c];
+    }
+    ctx->bvh_delta = bvh.delta;
+    ctx->n_static = n_static;
+    return GRCA_OK;
 }
 
 grca_status grca_set_ray_mask(grca_ctx* ctx, int32_t id, const uint32_t* bits, int where, void* stream) {
@@ -600,7 +667,7 @@ static void fill_sensor(const grca_ctx* ctx, int id, uint32_t ray_off, SensorDev
 static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, float* out_dist, uint32_t* out_tri,
                                 uint32_t flags, cudaStream_t st, CastArgs& a) {
     if (!ids || n < 1 || n > (uint32_t)MAX_SENSORS || !out_dist || !out_tri) return GRCA_ERR_INVALID_ARG;
-    if (flags & ~0x3Fu) return GRCA_ERR_INVALID_ARG;
+    if (flags & ~0xFFu) return GRCA_ERR_INVALID_ARG;
     if ((flags & GRCA_CAST_DUMP_CANDIDATES) && !ctx->dump) return GRCA_ERR_INVALID_ARG;
     for (uint32_t k = 0; k < n; ++k)
         if (ids[k] < 0 || ids[k] >= (int32_t)ctx->sensors.size()) return GRCA_ERR_INVALID_ARG;
@@ -686,11 +753,38 @@ static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, f
     a.surv_cap = (uint32_t)ctx->surv_cap;
     a.area_eps2 = (float)(ctx->opt.area_eps * ctx->opt.area_eps);
     a.post = post;
+    // GACP-T_g pays where a range limit empties whole groups; with unlimited
+    // range its elevation-only test rarely drops a 32-triangle group and
+    // would cost more than it saves, so it runs only when some sensor of the
+    // cast has a finite d_max
+    bool finite_range = false;
+    for (uint32_t k = 0; k < n; ++k) finite_range |= std::isfinite(ctx->sensors[ids[k]].d.d_max);
+    a.gbounds = (flags & GRCA_CAST_NO_GROUP_CULL) || !finite_range ? nullptr : ctx->d_gb;
+    // hybrid: static triangles through the hierarchy when it is current, the
+    // mode allows it and every sensor is close enough for its box inflation
+    bool hybrid = ctx->d_bvh_nodes && !ctx->bvh_stale && ctx->n_static &&
+                  !(flags & (GRCA_CAST_BRUTE | GRCA_CAST_LOSSY_AREA | GRCA_CAST_DUMP_CANDIDATES | GRCA_CAST_NO_STATIC_BVH));
+    for (uint32_t k = 0; hybrid && k < n; ++k) {
+        const grca_sensor_desc& d = ctx->sensors[ids[k]].d;
+        double far2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double e = std::max(std::fabs(ctx->bvh_lo[c] - d.origin[c]), std::fabs(ctx->bvh_hi[c] - d.origin[c]));
+            far2 += e * e;
+        }
+        const double t_far = std::min(std::sqrt(far2), d.d_max);
+        if (!(BVH_RAY_ETA * t_far <= ctx->bvh_delta)) hybrid = false;
+    }
+    if (hybrid) {
+        a.tri_first = ctx->n_static;
+        a.bvh_nodes = ctx->d_bvh_nodes;
+        a.bvh_prim = ctx->d_bvh_prim;
+        a.bvh_tris = ctx->d_bvh_tris;
+    }
     return GRCA_OK;
 }
 
 static LaunchCfg cfg_for(grca_ctx* ctx, const CastArgs& a) {
-    auto key = std::make_tuple(a.n_sensors, a.n_rays_total, a.n_tris, a.flags & 0x27u);
+    auto key = std::make_tuple(a.n_sensors, a.n_rays_total, a.n_tris - a.tri_first, a.flags & 0xE7u);
     auto it = ctx->tuned.find(key);
     return it == ctx->tuned.end() ? ctx->cfg : it->second;
 }
@@ -698,19 +792,34 @@ static LaunchCfg cfg_for(grca_ctx* ctx, const CastArgs& a) {
 static grca_status run_frame(grca_ctx* ctx, CastArgs& a, const LaunchCfg& cfg, cudaStream_t st, bool use_graph) {
     a.inline_max = (uint32_t)cfg.inline_max;
     a.chunk_rays = (uint32_t)cfg.chunk_rays;
+    const uint32_t pending = ctx->pending_launches;
+    ctx->pending_launches = 0;
     if (ctx->profiling) {
         KernelMarks mk{profile_mark, ctx};
-        ctx->last_launches = (uint32_t)launch_frame(a, cfg, ctx->n_sm, st, &mk);
+        ctx->last_launches = pending + (uint32_t)launch_frame(a, cfg, ctx->n_sm, st, &mk);
         CK(cudaGetLastError());
         return GRCA_OK;
     }
     if (!use_graph) {
-        ctx->last_launches = (uint32_t)launch_frame(a, cfg, ctx->n_sm, st);
+        ctx->last_launches = pending + (uint32_t)launch_frame(a, cfg, ctx->n_sm, st);
         CK(cudaGetLastError());
         return GRCA_OK;
     }
-    GraphKey k{a.n_sensors, a.n_rays_total, a.total_ch, a.flags | (a.post ? 0x80000000u : 0u), a.n_tris, a.out_dist, a.out_tri, a.tris, a.keys,
-               a.dump, cfg.cull_block, cfg.cull_blocks_per_sm, cfg.inline_max, cfg.chunk_rays};
+    GraphKey k{a.n_sensors,
+               a.n_rays_total,
+               a.total_ch,
+               a.flags | (a.post ? 0x80000000u : 0u) | (a.gbounds ? 0x40000000u : 0u),
+               a.n_tris,
+               a.bvh_nodes ? a.tri_first : 0xFFFFFFFFu,
+               a.out_dist,
+               a.out_tri,
+               a.tris,
+               a.keys,
+               a.dump,
+               cfg.cull_block,
+               cfg.cull_blocks_per_sm,
+               cfg.inline_max,
+               cfg.chunk_rays};
     auto it = ctx->graphs.find(k);
     if (it == ctx->graphs.end()) {
         if (ctx->graphs.size() >= 32) free_graphs(ctx);
@@ -723,10 +832,10 @@ static grca_status run_frame(grca_ctx* ctx, CastArgs& a, const LaunchCfg& cfg, c
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
-        it = ctx->graphs.emplace(k, exec).first;
-        ctx->last_launches = (uint32_t)nl;
+        it = ctx->graphs.emplace(k, std::make_pair(exec, nl)).first;
     }
-    CK(cudaGraphLaunch(it->second, st));
+    ctx->last_launches = pending + (uint32_t)it->second.second;
+    CK(cudaGraphLaunch(it->second.first, st));
     return GRCA_OK;
 }
 
@@ -802,6 +911,9 @@ grca_status grca_get_stats(grca_ctx* ctx, grca_stats* out, void* stream) {
     out->ties = c[C_TIES];
     out->flagged_rays = c[C_FLAGGED];
     out->recheck_pairs = c[C_RECHECK];
+    out->group_culled = c[C_GROUP];
+    out->bvh_node_visits = c[C_BVH_VISITS];
+    out->bvh_tests = c[C_BVH_TESTS];
     out->n_rays = ctx->last_n_rays;
     out->device_error = err;
     return err ? GRCA_ERR_CAPACITY : GRCA_OK;

@@ -2,6 +2,8 @@
 // kernels (grca_kernels.cu).  Not part of the public ABI.
 #pragma once
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 namespace grca {
@@ -22,7 +24,7 @@ enum { Q_BIG = 0, Q_CHUNK = 1, Q_RECHECK = 2, Q_FLAG = 3, Q_DUMP = 4, Q_SURV = 5
 // statistics counters (device u64[16])
 enum {
     C_PAIRS = 0, C_PAIRS_LIVE, C_CAND, C_CAND_INLINE, C_BIG, C_CHUNKS, C_TESTS, C_HITS,
-    C_UNCERTAIN, C_TIES, C_FLAGGED, C_RECHECK, C_SURV, C_NUM = 16
+    C_UNCERTAIN, C_TIES, C_FLAGGED, C_RECHECK, C_SURV, C_GROUP, C_BVH_VISITS, C_BVH_TESTS, C_NUM = 16
 };
 // device error bits
 enum { ERR_BIG_CAP = 1, ERR_CHUNK_CAP = 2, ERR_RECHECK_CAP = 4, ERR_FLAG_CAP = 8, ERR_DUMP_CAP = 16, ERR_SURV_CAP = 32 };
@@ -146,6 +148,13 @@ struct CastArgs {
     uint32_t surv_cap;
     float area_eps2;           // eps_A^2 of the lossy apparent-area cull (flag bit 5)
     uint32_t post;             // 1: some sensor of the cast has a ray mask or range noise
+    const float4* gbounds;     // per 32-triangle group: box lo (xyz, pad), hi (xyz, pad); nullptr: no group cull
+    // hybrid static/dynamic pipeline: triangles [0, tri_first) are traced
+    // through the static hierarchy, [tri_first, n_tris) go through the culls
+    uint32_t tri_first;
+    const struct BvhNode* bvh_nodes;  // nullptr: no static hierarchy in this cast
+    const uint32_t* bvh_prim;         // leaf order -> triangle id
+    const float* bvh_tris;            // vertices in leaf order (9 floats each)
 };
 
 struct LaunchCfg {
@@ -158,7 +167,8 @@ struct LaunchCfg {
 
 // kernels of one frame, in launch order
 enum {
-    K_INIT = 0, K_CULL_A, K_CULL_B, K_EXPAND, K_TEST, K_RECHECK_FILTER, K_RECHECK_RAYS, K_RECHECK_PAIRS, K_DECODE, K_NUM
+    K_INIT = 0, K_CULL_A, K_CULL_B, K_EXPAND, K_TEST, K_BVH, K_RECHECK_FILTER, K_RECHECK_RAYS, K_RECHECK_PAIRS, K_DECODE,
+    K_NUM
 };
 extern const char* const kKernelNames[K_NUM];
 
@@ -173,6 +183,48 @@ struct KernelMarks {
 int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t st,
                  const KernelMarks* marks = nullptr);
 size_t cull_smem_bytes(const CastArgs& a, const LaunchCfg& cfg);  // fused k_cull
-// launch the fused culling kernel (allocation-free path)
+
+// ---------------------------------------------------------------------------
+// static hierarchy (hybrid static/dynamic pipeline)
+// ---------------------------------------------------------------------------
+// A binary node holds both children's boxes (lo xyz, hi xyz) and references:
+// >= 0 an inner node, < 0 a leaf of at most BVH_LEAF_MAX triangles in leaf
+// order: bit 31 set, first << 3, count - 1 in the low 3 bits.
+struct BvhNode {
+    float c0lo_x, c0lo_y, c0lo_z, c0hi_x, c0hi_y, c0hi_z;
+    float c1lo_x, c1lo_y, c1lo_z, c1hi_x, c1hi_y, c1hi_z;
+    int32_t child0, child1, pad0, pad1;
+};
+static_assert(sizeof(BvhNode) == 64, "one node = four 16-byte loads");
+constexpr uint32_t BVH_LEAF_MAX = 8;
+constexpr int BVH_STACK = 64;
+// Boxes are inflated outward by delta = BVH_ETA * (scene diagonal + 1).  A
+// candidate that the FP32 test can report as a hit or send to the FP64
+// re-test lies within ~2e-6 t of the FP32 ray at distance t (table and
+// rotation rounding of the direction, the test's error bounds), so the
+// traversal is exact for sensors whose farthest scene point is within
+// delta / 4e-6 = 1.25 scene diagonals; casts from farther sensors trace the
+// static triangles through the culls instead.
+constexpr double BVH_ETA = 5e-6;
+constexpr double BVH_RAY_ETA = 4e-6;
+__host__ __device__ constexpr int32_t bvh_leaf_ref(uint32_t first, uint32_t count) {
+    return (int32_t)(0x80000000u | (first << 3) | (count - 1u));
+}
+struct BvhHost {
+    std::vector<BvhNode> nodes;
+    std::vector<uint32_t> prim;
+    float scene_lo[3] = {0, 0, 0}, scene_hi[3] = {0, 0, 0};
+    double delta = 0.0;
+    int depth = 0;
+};
+// host build over n triangles (9 floats each); false if the tree is too deep
+bool build_bvh(const float* tris, uint32_t n, BvhHost& out);
+void launch_bvh(const CastArgs& a, int n_sm, cudaStream_t st);
+
+// GACP-T_g group bounds: the axis-aligned box of every 32-triangle group that
+// overlaps triangles [first, first + n) (lo.xyz, 0 then hi.xyz, 0 per group)
+constexpr uint32_t GROUP_TRIS = 32;
+void launch_group_bounds(const float* tris, uint32_t n_tris, uint32_t first, uint32_t n, float4* gb, int n_sm,
+                         cudaStream_t st);
 
 }  // namespace grca

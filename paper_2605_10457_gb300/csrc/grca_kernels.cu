@@ -173,6 +173,13 @@ __device__ __forceinline__ void make_setup(const SensorDev& S, const TriW& T, co
     out.set(20, U32 * (fabsf(S.B[6]) * q0 + fabsf(S.B[7]) * q1 + fabsf(S.B[8]) * q2 + 6.f * fabsf(ne.z)));
 }
 
+// FP32 error bound of det = w0.n used by the back-face cull (n = (v1-v0)x(v2-v0),
+// N the sums of |products| of its cross-product terms)
+__device__ __forceinline__ float backface_err(const V3& w0, const V3& n, const V3& N) {
+    return U32 * (fabsf(w0.x) * (3.f * N.x + 4.f * fabsf(n.x)) + fabsf(w0.y) * (3.f * N.y + 4.f * fabsf(n.y)) +
+                  fabsf(w0.z) * (3.f * N.z + 4.f * fabsf(n.z)));
+}
+
 __device__ __forceinline__ float det_error(const V3& w0, const TriW& T) {
     return U32 * (fabsf(w0.x) * (3.f * T.N.x + 4.f * fabsf(T.n.x)) + fabsf(w0.y) * (3.f * T.N.y + 4.f * fabsf(T.n.y)) +
                   fabsf(w0.z) * (3.f * T.N.z + 4.f * fabsf(T.n.z))) + 1e-35f;
@@ -207,6 +214,15 @@ struct SetupSoA {
     const float* base;  // [SETUP_FIELDS][32]
     uint32_t i;
     __device__ __forceinline__ float f(int k) const { return base[k * 32 + i]; }
+};
+
+struct SetupReg {
+    float f_[SETUP_FIELDS];
+    __device__ __forceinline__ float f(int k) const { return f_[k]; }
+};
+struct SetupWriterReg {
+    SetupReg& r;
+    __device__ __forceinline__ void set(int k, float v) { r.f_[k] = v; }
 };
 
 template <bool RECHECK, typename SV>
@@ -729,17 +745,26 @@ __device__ __forceinline__ bool cull_elevation(const SensorDev& S, const T* ch, 
     if (cull_back) {
         float det = vdot(w0, nw);
         V3 e1 = vsub(v[1], v[0]), e2 = vsub(v[2], v[0]);
-        float Nx = fabsf(e1.y * e2.z) + fabsf(e1.z * e2.y), Ny = fabsf(e1.z * e2.x) + fabsf(e1.x * e2.z),
-              Nz = fabsf(e1.x * e2.y) + fabsf(e1.y * e2.x);
-        float err = U32 * (fabsf(w0.x) * (3.f * Nx + 4.f * fabsf(nw.x)) + fabsf(w0.y) * (3.f * Ny + 4.f * fabsf(nw.y)) +
-                           fabsf(w0.z) * (3.f * Nz + 4.f * fabsf(nw.z)));
-        if (det > 0.f && (!RECHECK || det > err)) return false;  // facing <=> det < 0
+        const V3 N = {fabsf(e1.y * e2.z) + fabsf(e1.z * e2.y), fabsf(e1.z * e2.x) + fabsf(e1.x * e2.z),
+                      fabsf(e1.x * e2.y) + fabsf(e1.y * e2.x)};
+        if (det > 0.f && (!RECHECK || det > backface_err(w0, nw, N))) return false;  // facing <=> det < 0
     }
     if (BRUTE) {
         span = pack_span(0, (int)S.n_ch - 1, false);
         return true;
     }
     const V3 wv[3] = {w0, rel_origin(S, v[1]), rel_origin(S, v[2])};
+    if (S.d_max < INFINITY) {
+        // range pre-cull (App. A.4.1 Step 1), only where provably empty: the
+        // farthest vertex inside d_min, or every point beyond d_max (each point
+        // lies within the longest edge of every vertex); skipped for unlimited
+        // range, where a d_min of centimetres would almost never drop a pair
+        const float r0 = vdot(wv[0], wv[0]), r1 = vdot(wv[1], wv[1]), r2 = vdot(wv[2], wv[2]);
+        const float dlo = fmaxf(S.d_min * (1.f - 2e-5f) - 2e-6f, 0.f);
+        if (fmaxf(r0, fmaxf(r1, r2)) < dlo * dlo) return false;
+        const float near = sqrtf(fminf(r0, fminf(r1, r2))) - sqrtf(fmaxf(eeT[0], fmaxf(eeT[1], eeT[2])));
+        if (near > S.d_max * (1.f + 2e-5f) + 2e-6f) return false;  // false for d_max = +inf
+    }
     if (lossy_area) {
         // Eq. apparent_area: A_T (c-o).n^ = (c-o).n / 2 with n = (v1-v0)x(v2-v0)
         V3 wc = {(wv[0].x + wv[1].x + wv[2].x) * (1.f / 3.f), (wv[0].y + wv[1].y + wv[2].y) * (1.f / 3.f),
@@ -1049,6 +1074,96 @@ __device__ __forceinline__ void flush_survivors(const CastArgs& a, CullAWarpSmem
     fill = 0;
 }
 
+// ---------------------------------------------------------------------------
+// GACP-T_g (Sec. 10.1.1): the emitter test lifted from one triangle to the
+// bounding box of a 32-triangle group.  A group is dropped for a sensor when
+// the box lies wholly beyond the range limits or when the elevation range of
+// its bounding sphere, seen from the sensor, holds no channel.  Every member's
+// own (padded) elevation range lies inside the sphere's, so the group test
+// never drops a pair that the per-triangle cull would keep.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool group_may_hit(const SensorDev& S, const float* sins, const uint16_t* lut,
+                                              const float4& lo, const float4& hi) {
+    // rounding of w = (v - o_hi) - o_lo is monotone in v, so every member
+    // vertex, transformed like the triangles, lies inside [wl, wh]
+    const V3 wl = rel_origin(S, V3{lo.x, lo.y, lo.z}), wh = rel_origin(S, V3{hi.x, hi.y, hi.z});
+    if (S.has_range) {
+        const float nx = fmaxf(fmaxf(wl.x, -wh.x), 0.f), ny = fmaxf(fmaxf(wl.y, -wh.y), 0.f),
+                    nz = fmaxf(fmaxf(wl.z, -wh.z), 0.f);
+        const float dmax = S.d_max * (1.f + 3e-5f) + 3e-6f;  // d_max may be +inf
+        if (nx * nx + ny * ny + nz * nz > dmax * dmax) return false;
+        const float fx = fmaxf(fabsf(wl.x), fabsf(wh.x)), fy = fmaxf(fabsf(wl.y), fabsf(wh.y)),
+                    fz = fmaxf(fabsf(wl.z), fabsf(wh.z));
+        const float dmin = fmaxf(S.d_min * (1.f - 3e-5f) - 3e-6f, 0.f);
+        if (fx * fx + fy * fy + fz * fz < dmin * dmin) return false;
+    }
+    const V3 c = {0.5f * (wl.x + wh.x), 0.5f * (wl.y + wh.y), 0.5f * (wl.z + wh.z)};
+    const V3 h = {0.5f * (wh.x - wl.x), 0.5f * (wh.y - wl.y), 0.5f * (wh.z - wl.z)};
+    const float R = sqrtf(vdot(h, h)) * (1.f + 1e-6f) + 2e-7f * (fabsf(c.x) + fabsf(c.y) + fabsf(c.z));
+    const float D2 = vdot(c, c);
+    // near or large spheres (half-angle above ~82 deg): keep, the bound is loose there
+    if (!(D2 > 0.f) || R * R > 0.98f * D2) return true;
+    const float invD = rsqrtf(D2);
+    // centre elevation from the sensor frame (no cancellation near the poles)
+    const float cx = S.B[0] * c.x + S.B[1] * c.y + S.B[2] * c.z, cy = S.B[3] * c.x + S.B[4] * c.y + S.B[5] * c.z,
+                cz = S.B[6] * c.x + S.B[7] * c.y + S.B[8] * c.z;
+    const float sphi = fminf(fmaxf(cz * invD, -1.f), 1.f);
+    const float cphi = fminf(sqrtf(cx * cx + cy * cy) * invD, 1.f);
+    const float sa = R * invD, ca = sqrtf(fmaxf(1.f - sa * sa, 0.f));
+    // elevation range of the cap of half-angle alpha around the centre direction
+    const float shi = (cphi * ca - sphi * sa < 0.f) ? 1.f : sphi * ca + cphi * sa;
+    const float slo = (cphi * ca + sphi * sa < 0.f) ? -1.f : sphi * ca - cphi * sa;
+    constexpr float PAD = 3e-5f;  // > FP32 error of this bound + the per-triangle padding
+    const int jl = chan_lower(S, sins, lut, slo - PAD);
+    return jl < (int)S.n_ch && sin_at(sins, jl) <= shi + PAD;
+}
+
+// one warp per 32-triangle group: box of its (present) vertices
+__global__ void k_group_bounds(const float* __restrict__ tris, uint32_t n_tris, uint32_t g0, uint32_t g1,
+                               float4* __restrict__ gb) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t g = g0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); g < g1; g += n_warps) {
+        const uint32_t t = g * GROUP_TRIS + lane;
+        float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+        if (t < n_tris) {
+            const float* v = tris + 9ull * t;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float x = __ldg(v + 3 * k), y = __ldg(v + 3 * k + 1), z = __ldg(v + 3 * k + 2);
+                lx = fminf(lx, x);
+                ly = fminf(ly, y);
+                lz = fminf(lz, z);
+                hx = fmaxf(hx, x);
+                hy = fmaxf(hy, y);
+                hz = fmaxf(hz, z);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+            ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+            lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+            hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+            hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+            hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+        }
+        if (lane == 0) {
+            gb[2ull * g] = make_float4(lx, ly, lz, 0.f);
+            gb[2ull * g + 1] = make_float4(hx, hy, hz, 0.f);
+        }
+    }
+}
+
+void launch_group_bounds(const float* tris, uint32_t n_tris, uint32_t first, uint32_t n, float4* gb, int n_sm,
+                         cudaStream_t st) {
+    if (n == 0 || n_tris == 0) return;
+    const uint32_t g0 = first / GROUP_TRIS, g1 = (uint32_t)(((uint64_t)first + n + GROUP_TRIS - 1) / GROUP_TRIS);
+    const uint32_t warps = g1 - g0;
+    const uint32_t blocks = std::min<uint32_t>((warps + 7) / 8, (uint32_t)n_sm * 8u);
+    k_group_bounds<<<std::max(blocks, 1u), 256, 0, st>>>(tris, n_tris, g0, g1, gb);
+}
+
 // prologue of k_cull_a: sensor descriptors, channel sines and lookup tables
 struct CullASmem {
     SensorDev* sens;
@@ -1075,7 +1190,7 @@ __device__ __forceinline__ CullASmem cull_a_prologue(const CastArgs& a, unsigned
     return m;
 }
 
-template <bool RECHECK, bool BRUTE>
+template <bool RECHECK, bool BRUTE, bool GROUPS>
 __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     CullASmem M = cull_a_prologue(a, smem);
@@ -1086,10 +1201,34 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
     uint32_t fill = 0;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t gwarp = ((blockIdx.x * blockDim.x) >> 5) + wib;
-    for (uint32_t base = gwarp * 32; base < a.n_tris; base += n_warps * 32) {
+    constexpr bool groups = GROUPS && !BRUTE;
+    uint32_t g_culled = 0;
+    // triangles [0, tri_first) belong to the static hierarchy in a hybrid cast
+    const uint32_t first = a.tri_first, base0 = first & ~31u;
+    for (uint32_t base = base0 + gwarp * 32; base < a.n_tris; base += n_warps * 32) {
         const uint32_t cnt = min(32u, a.n_tris - base);
+        const uint32_t skip = first > base ? first - base : 0u;  // leading lanes outside the range
+        unsigned long long live = ~0ull;
+        if (groups) {
+            // GACP-T_g: lane s tests sensor s against the group's box
+            const float4 lo = __ldg(&a.gbounds[2u * (base / GROUP_TRIS)]);
+            const float4 hi = __ldg(&a.gbounds[2u * (base / GROUP_TRIS) + 1u]);
+            live = 0;
+            for (uint32_t s0 = 0; s0 < a.n_sensors; s0 += 32) {
+                const uint32_t sn = s0 + lane;
+                const bool ok = sn < a.n_sensors &&
+                                group_may_hit(M.sens[sn], M.sins + M.sens[sn].ch_loc, M.lut + sn * LUT_BINS, lo, hi);
+                live |= (unsigned long long)__ballot_sync(0xffffffffu, ok) << s0;
+            }
+            g_culled += (a.n_sensors - (uint32_t)__popcll(live)) * (cnt - skip);
+            if (g_culled >= 0x40000000u && lane == 0) {
+                atomicAdd(&a.counters[C_GROUP], (unsigned long long)g_culled);
+                g_culled = 0;
+            }
+            if (live == 0) continue;  // the whole tile: no load, no per-triangle work
+        }
         stage_tris(a, base, cnt, W.tri, lane);
-        bool valid = lane < cnt;
+        bool valid = lane < cnt && lane >= skip;
         const float* t9 = W.tri + 9 * (valid ? lane : 0);
         V3 v[3] = {{t9[0], t9[1], t9[2]}, {t9[3], t9[4], t9[5]}, {t9[6], t9[7], t9[8]}};
         V3 nw = vcross(vsub(v[1], v[0]), vsub(v[2], v[0]));
@@ -1104,6 +1243,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
             const uint32_t ng = min((uint32_t)CULL_A_GROUP, a.n_sensors - sg);
             if (fill + 32 * CULL_A_GROUP > SURV_BUF) flush_survivors(a, W, fill, lane, a.n_sensors);
             for (uint32_t k = 0; k < ng; ++k) {
+                if (!((live >> (sg + k)) & 1ull)) continue;  // warp-uniform
                 uint32_t span = 0;
                 const SensorDev& S = M.sens[sg + k];
                 bool ok = valid && cull_elevation<RECHECK, BRUTE>(S, M.sins + S.ch_loc, M.lut + (sg + k) * LUT_BINS, v,
@@ -1119,6 +1259,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
         }
     }
     flush_survivors(a, W, fill, lane, a.n_sensors);
+    if (groups && lane == 0 && g_culled) atomicAdd(&a.counters[C_GROUP], (unsigned long long)g_culled);
 }
 
 // ---------------------------------------------------------------------------
@@ -1708,7 +1849,121 @@ __global__ void k_decode(CastArgs a, int recheck) {
         a.out_dist[g] = dist;
         a.out_tri[g] = id;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_PAIRS] = (unsigned long long)a.n_tris * a.n_sensors;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        a.counters[C_PAIRS] = (unsigned long long)(a.n_tris - a.tri_first) * a.n_sensors;
+}
+
+// ---------------------------------------------------------------------------
+// k_bvh: the static side of the hybrid static/dynamic pipeline (Sec. 7).
+// One thread per ray walks the static hierarchy front to back (both child
+// boxes per node, the nearer child first, the farther one on a per-thread
+// stack).  Each leaf triangle takes the same pair setup, FP32 test and
+// closest-hit commit as the culled path, into the same u64 keys, so the
+// static and dynamic results merge on the GPU by the key minimum.  Subtrees
+// that start beyond the ray's best certain hit (dynamic or static, plus the
+// tie band) are skipped.
+// ---------------------------------------------------------------------------
+template <bool RECHECK>
+__global__ void __launch_bounds__(128, 4) k_bvh(CastArgs a) {
+    const bool cull_back = a.flags & 2u;
+    uint32_t n_vis = 0, n_tst = 0, c_unc = 0, c_ties = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    int32_t stack[BVH_STACK];
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_rays_total; g += stride) {
+        uint32_t sn = 0;
+        for (uint32_t k = 1; k < a.n_sensors; ++k)
+            if (a.sensors[k].ray_off <= g) sn = k;
+        const SensorDev& S = a.sensors[sn];
+        const uint32_t q = g - S.ray_off;
+        const uint32_t j = q / S.n_rays, i = q - j * S.n_rays;
+        const V3 d = ray_dir(__ldg(&a.ch_sc[S.ch_off + j]), __ldg(&a.az_sc[S.az_off + i]));
+        // world direction B^T d for the box tests (the triangle test uses d)
+        const V3 dw = {S.B[0] * d.x + S.B[3] * d.y + S.B[6] * d.z, S.B[1] * d.x + S.B[4] * d.y + S.B[7] * d.z,
+                       S.B[2] * d.x + S.B[5] * d.y + S.B[8] * d.z};
+        const V3 inv = {1.f / (dw.x != 0.f ? dw.x : 1e-30f), 1.f / (dw.y != 0.f ? dw.y : 1e-30f),
+                        1.f / (dw.z != 0.f ? dw.z : 1e-30f)};
+        const V3 o = {S.o_hi[0], S.o_hi[1], S.o_hi[2]};
+        unsigned long long cur = __ldcg(&a.keys[g]);
+        const float tmin = fmaxf(S.d_min * (1.f - 2e-5f) - 2e-6f, 0.f);
+        float tmax = fminf(S.d_max * (1.f + 2e-5f) + 2e-6f, __uint_as_float((uint32_t)(cur >> 32)) * (1.f + 4.f * BETA));
+        int sp = 0;
+        int32_t node = 0;
+        while (true) {
+            if (node >= 0) {
+                const float4* np = reinterpret_cast<const float4*>(a.bvh_nodes + node);
+                const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2);
+                const int4 n3 = __ldg(reinterpret_cast<const int4*>(np) + 3);
+                n_vis++;
+                // slab distances (x - o) / dw; the boxes are inflated to absorb the rounding
+                const float ax0 = (n0.x - o.x) * inv.x, bx0 = (n0.w - o.x) * inv.x;
+                const float ay0 = (n0.y - o.y) * inv.y, by0 = (n1.x - o.y) * inv.y;
+                const float az0 = (n0.z - o.z) * inv.z, bz0 = (n1.y - o.z) * inv.z;
+                const float ax1 = (n1.z - o.x) * inv.x, bx1 = (n2.y - o.x) * inv.x;
+                const float ay1 = (n1.w - o.y) * inv.y, by1 = (n2.z - o.y) * inv.y;
+                const float az1 = (n2.x - o.z) * inv.z, bz1 = (n2.w - o.z) * inv.z;
+                const float tn0 = fmaxf(fmaxf(fminf(ax0, bx0), fminf(ay0, by0)), fmaxf(fminf(az0, bz0), tmin));
+                const float tf0 = fminf(fminf(fmaxf(ax0, bx0), fmaxf(ay0, by0)), fminf(fmaxf(az0, bz0), tmax));
+                const float tn1 = fmaxf(fmaxf(fminf(ax1, bx1), fminf(ay1, by1)), fmaxf(fminf(az1, bz1), tmin));
+                const float tf1 = fminf(fminf(fmaxf(ax1, bx1), fmaxf(ay1, by1)), fminf(fmaxf(az1, bz1), tmax));
+                const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
+                if (h0 && h1) {
+                    const bool swap = tn1 < tn0;
+                    stack[sp++] = swap ? n3.x : n3.y;  // depth < BVH_STACK (checked at build)
+                    node = swap ? n3.y : n3.x;
+                } else if (h0 || h1) {
+                    node = h0 ? n3.x : n3.y;
+                } else {
+                    if (sp == 0) break;
+                    node = stack[--sp];
+                }
+                continue;
+            }
+            const uint32_t lf = ((uint32_t)node >> 3) & 0x0FFFFFFFu, cnt = ((uint32_t)node & 7u) + 1u;
+            for (uint32_t k = lf; k < lf + cnt; ++k) {
+                float t9[9];
+#pragma unroll
+                for (int m = 0; m < 9; ++m) t9[m] = __ldg(a.bvh_tris + 9ull * k + m);
+                TriW T;
+                tri_world(t9, T);
+                if (T.n.x == 0.f && T.n.y == 0.f && T.n.z == 0.f) continue;  // zero area: never hit
+                V3 w[3], p[3];
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk) {
+                    w[kk] = rel_origin(S, T.v[kk]);
+                    p[kk] = rotB(S.B, w[kk]);
+                }
+                const float det = vdot(w[0], T.n);
+                if (cull_back && det > 0.f && (!RECHECK || det > backface_err(w[0], T.n, T.N))) continue;
+                const float err_det = det_error(w[0], T);
+                if (!(det != 0.f || (RECHECK && fabsf(det) <= err_det))) continue;
+                SetupReg sr;
+                make_setup(S, T, w, p, det, err_det, SetupWriterReg{sr});
+                float t, terr;
+                const int res = test_fp32<RECHECK>(sr, S, d, t, terr);
+                n_tst++;
+                if (res == T_MISS) continue;
+                const uint32_t tri = __ldg(a.bvh_prim + k);
+                commit_pre<RECHECK>(a, g, tri, res, t, terr, cur, c_unc, c_ties);
+                if (res == T_HIT) {
+                    const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | tri;
+                    if (key < cur) cur = key;
+                    tmax = fminf(tmax, t * (1.f + 4.f * BETA));
+                }
+            }
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    n_vis = __reduce_add_sync(0xffffffffu, n_vis);
+    n_tst = __reduce_add_sync(0xffffffffu, n_tst);
+    c_unc = __reduce_add_sync(0xffffffffu, c_unc);
+    c_ties = __reduce_add_sync(0xffffffffu, c_ties);
+    if ((threadIdx.x & 31u) == 0) {
+        if (n_vis) atomicAdd(&a.counters[C_BVH_VISITS], (unsigned long long)n_vis);
+        if (n_tst) atomicAdd(&a.counters[C_BVH_TESTS], (unsigned long long)n_tst);
+        if (c_unc) atomicAdd(&a.counters[C_UNCERTAIN], (unsigned long long)c_unc);
+        if (c_ties) atomicAdd(&a.counters[C_TIES], (unsigned long long)c_ties);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1734,20 +1989,25 @@ static void ensure_smem_attr(K kernel, size_t smem) {
     if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-const char* const kKernelNames[K_NUM] = {"k_init",           "k_cull_a",       "k_cull_b",
-                                          "k_expand",         "k_test",         "k_recheck_filter",
-                                          "k_recheck_rays",   "k_recheck_pairs", "k_decode"};
+const char* const kKernelNames[K_NUM] = {"k_init",  "k_cull_a",         "k_cull_b",       "k_expand",
+                                         "k_test",  "k_bvh",            "k_recheck_filter", "k_recheck_rays",
+                                         "k_recheck_pairs", "k_decode"};
 
 template <bool R, bool B>
 static void launch_cull_split(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t st,
                               const std::function<void(int, int)>& mark) {
     size_t sa = cull_a_smem_bytes(a, cfg), sb = cull_b_smem_bytes(a);
-    ensure_smem_attr(k_cull_a<R, B>, sa);
+    const bool groups = !B && a.gbounds != nullptr;
+    ensure_smem_attr(k_cull_a<R, B, false>, sa);
+    if (groups) ensure_smem_attr(k_cull_a<R, B, true>, sa);
     ensure_smem_attr(k_cull_b<R, B>, sb);
-    uint32_t max_blocks = (a.n_tris + cfg.cull_block - 1) / cfg.cull_block;
+    uint32_t max_blocks = (a.n_tris - (a.tri_first & ~31u) + cfg.cull_block - 1) / cfg.cull_block;
     int grid_a = (int)std::min<uint32_t>(std::max<uint32_t>(max_blocks, 1u), (uint32_t)(n_sm * cfg.cull_blocks_per_sm));
     mark(K_CULL_A, 0);
-    k_cull_a<R, B><<<grid_a, cfg.cull_block, sa, st>>>(a);
+    if (groups)
+        k_cull_a<R, B, true><<<grid_a, cfg.cull_block, sa, st>>>(a);
+    else
+        k_cull_a<R, B, false><<<grid_a, cfg.cull_block, sa, st>>>(a);
     mark(K_CULL_A, 1);
     mark(K_CULL_B, 0);
     k_cull_b<R, B><<<n_sm * cfg.cull_blocks_per_sm * 2, 256, sb, st>>>(a);
@@ -1786,6 +2046,18 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
             k_test<false><<<n_sm * 8, cfg.test_block, 0, st>>>(a);
         mark(K_TEST, 1);
         launches += 2;
+    }
+    if (a.bvh_nodes) {
+        // static side of a hybrid cast, after the dynamic triangles so that
+        // their hits bound the traversal
+        const int blocks = (int)std::min<uint32_t>((a.n_rays_total + 127) / 128, (uint32_t)n_sm * 16);
+        mark(K_BVH, 0);
+        if (recheck)
+            k_bvh<true><<<std::max(blocks, 1), 128, 0, st>>>(a);
+        else
+            k_bvh<false><<<std::max(blocks, 1), 128, 0, st>>>(a);
+        mark(K_BVH, 1);
+        launches++;
     }
     if (recheck) {
         mark(K_RECHECK_FILTER, 0);

@@ -23,6 +23,8 @@ CAST_BRUTE = 1 << 2
 CAST_GRAPH = 1 << 3
 CAST_DUMP_CANDIDATES = 1 << 4
 CAST_LOSSY_AREA = 1 << 5
+CAST_NO_GROUP_CULL = 1 << 6
+CAST_NO_STATIC_BVH = 1 << 7
 NO_HIT = 0xFFFFFFFF
 
 
@@ -45,7 +47,8 @@ class grca_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("pairs", "pairs_live", "survivors", "candidates", "candidates_inline",
                                                "big_pairs",
                                                "chunks", "tests", "hits", "uncertain", "ties", "flagged_rays",
-                                               "recheck_pairs", "n_rays")] + \
+                                               "recheck_pairs", "group_culled", "bvh_node_visits", "bvh_tests",
+                                               "n_rays")] + \
                [("device_error", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
     def as_dict(self):
@@ -63,7 +66,7 @@ EXPORTS = ["grca_create", "grca_destroy", "grca_create_sensor", "grca_set_sensor
            "grca_update_vertices", "grca_cast", "grca_cast_host", "grca_autotune", "grca_set_debug_dump",
            "grca_get_stats", "grca_last_launch_count", "grca_profile_enable", "grca_profile_read",
            "grca_status_string", "grca_last_cuda_error", "grca_cast_noalloc",
-           "grca_set_ray_mask", "grca_set_sensor_azimuths", "grca_set_range_noise"]
+           "grca_set_ray_mask", "grca_set_sensor_azimuths", "grca_set_range_noise", "grca_build_static"]
 
 
 def library_path() -> str:
@@ -110,6 +113,8 @@ def _lib_handle(build_if_missing: bool = True):
     lib.grca_profile_read.argtypes = [P, u32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_uint64),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32)]
     lib.grca_profile_read.restype = i32
+    lib.grca_build_static.argtypes = [P, u32, P]
+    lib.grca_build_static.restype = i32
     lib.grca_set_ray_mask.argtypes = [P, i32, P, ctypes.c_int, P]
     lib.grca_set_ray_mask.restype = i32
     lib.grca_set_sensor_azimuths.argtypes = [P, i32, P]
@@ -220,6 +225,10 @@ class Caster:
         if az is not None:
             self.set_azimuths(sid.value, az)
         return sid.value
+
+    def build_static(self, n_static: int, stream=None):
+        """Hybrid pipeline: static hierarchy over triangles [0, n_static) (0 drops it)."""
+        self._check(self.lib.grca_build_static(self.ctx, int(n_static), _stream_ptr(stream)), "grca_build_static")
 
     def set_azimuths(self, sid: int, theta=None):
         """Per-ray azimuths (radians) replacing the uniform grid; None restores it."""
