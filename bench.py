@@ -36,9 +36,33 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mrays/s and ms/frame (8x128x4096 LiDARs, 22M tris), batched vs plain, oracle-exact"
 F_CULL_A = 100.0  # FP32 flops per (triangle, sensor) pair: transform + elevation range + channel search
-F_CULL_B = 100.0  # FP32 flops per surviving pair: emitter frame + azimuth range + ray interval (+ setup)
+F_CULL_B = 100.0  # FP32 flops per surviving pair: emitter frame + azimuth range + ray interval
+F_SETUP = 200.0   # FP32 flops per live pair: the test setup (edge normals, error bounds)
 F_TEST = 30.0     # FP32 flops per candidate ray-triangle test
 TRI_BYTES = 36.0
+ROOT = os.path.dirname(os.path.abspath(__file__))
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2605_10457_gb300", "csrc", f) for f in ("grca_kernels.cu", "grca_internal.h")]
+
+
+def kernels_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic_c5.json), or None when the kernel sources changed since."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "traffic_c5.json")))
+    except (OSError, ValueError):
+        return None
+    e = d.get("kernels", {}).get(kernel)
+    if not e or d.get("kernels_sha256") != kernels_digest():
+        return None
+    return e.get("dram_bytes_per_launch")
 
 
 def _peaks():
@@ -105,6 +129,28 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def frame_of(rank: int, ws: int, k: int, n_frames: int) -> int:
+    """Weak scaling over frames: step k of rank r casts frame (r + k * ws) mod n_frames,
+    so the ranks of one step cast distinct frames (ws <= n_frames)."""
+    return (rank + k * ws) % n_frames
+
+
+def max_over_ranks(value: float, ws: int, device=None) -> float:
+    """The slowest rank's time (all ranks get it); identity on one rank."""
+    if ws <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws: int, rays_per_step: int, steps: int, seconds: float) -> float:
+    """Whole-job Mrays/s: every rank casts rays_per_step rays per step."""
+    return ws * rays_per_step * steps / seconds / 1e6
 
 
 def cpu_oracle_rate(scene, tris, budget_s: float, seed: int = 0, max_rays: int = 1 << 20):
@@ -240,7 +286,7 @@ def main():
         tune_ms = c.autotune(ids, FL, out)
 
     def step_batched(k):
-        f = (rank + k * ws) % args.frames
+        f = frame_of(rank, ws, k, args.frames)
         c.update(frames_dev[f], ns)
         c.cast(ids, FL | grca.CAST_GRAPH, out)
 
@@ -249,7 +295,7 @@ def main():
     plain_out = [(out[0][offs[i]:offs[i + 1]], out[1][offs[i]:offs[i + 1]]) for i in range(len(ids))]
 
     def step_plain(k):
-        f = (rank + k * ws) % args.frames
+        f = frame_of(rank, ws, k, args.frames)
         c.update(frames_dev[f], ns)
         for i, sid in enumerate(ids):
             c.cast([sid], grca.CAST_GRAPH | (FL & grca.CAST_NO_GROUP_CULL), plain_out[i])
@@ -277,13 +323,7 @@ def main():
         if profiler_range:
             torch.cuda.profiler.stop()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1), ws, dev)
 
     # --- headline: batched FP32 + FP64 recheck, CUDA-graph replay -------------
     clk = Clocks(local)
@@ -293,7 +333,7 @@ def main():
     st = c.stats(check=False)
     if args.lean:
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": ws * n_rays * args.steps / (ms_b / 1e3) / 1e6,
+            print(json.dumps({"metric": METRIC, "value": whole_job_rate(ws, n_rays, args.steps, ms_b / 1e3),
                               "unit": "Mrays/s", "ms_per_step": ms_b / args.steps, "lean": True,
                               "stats": st, "clocks": clocks}), flush=True)
         c.close()
@@ -328,16 +368,11 @@ def main():
         c.cast_host_ptrs(ids_a, pin_frames[k % len(pin_frames)].data_ptr(), ns, nd, h_dist.data_ptr(),
                          h_tri.data_ptr(), FL | grca.CAST_GRAPH, sp)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
 
-    value = ws * n_rays * args.steps / (ms_b / 1e3) / 1e6
-    plain_value = ws * n_rays * args.steps / (ms_p / 1e3) / 1e6
-    e2e_value = ws * n_rays * e2e_steps / e2e_s / 1e6
+    value = whole_job_rate(ws, n_rays, args.steps, ms_b / 1e3)
+    plain_value = whole_job_rate(ws, n_rays, args.steps, ms_p / 1e3)
+    e2e_value = whole_job_rate(ws, n_rays, e2e_steps, e2e_s)
 
     # --- roofline of the dominant kernel ---------------------------------------
     peaks, src = _peaks()
@@ -350,7 +385,8 @@ def main():
     if dom_name == "k_cull_a":
         flops = pairs * F_CULL_A
     elif dom_name == "k_cull_b":
-        flops = st_prof["survivors"] * F_CULL_B + st_prof["candidates_inline"] * F_TEST
+        flops = (st_prof["survivors"] * F_CULL_B + st_prof["pairs_live"] * F_SETUP
+                 + st_prof["candidates_inline"] * F_TEST)
     elif dom_name == "k_test":
         flops = (st_prof["tests"] - st_prof["candidates_inline"]) * F_TEST
     else:
@@ -359,10 +395,11 @@ def main():
     ka = prof.get("k_cull_a", {"total_ms": 1.0, "launches": 1})
     hbm_achieved = (sc.n_tris * TRI_BYTES) / (ka["total_ms"] / max(1, ka["launches"]) / 1e3) / 1e9
     roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak if fp32_peak else None, "traffic": None,
+                "frac": achieved / fp32_peak if fp32_peak else None, "traffic": measured_traffic(dom_name),
                 "peak_source": f"FP32 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (unit counts and max clock)",
                 "algorithmic": {"k_cull_a": f"{F_CULL_A:.0f} flop per (tri, sensor) pair",
-                                "k_cull_b": f"{F_CULL_B:.0f} flop per surviving pair + {F_TEST:.0f} per inline test",
+                                "k_cull_b": f"{F_CULL_B:.0f} flop per surviving pair + {F_SETUP:.0f} per live pair "
+                                            f"(setup) + {F_TEST:.0f} per inline test",
                                 "k_test": f"{F_TEST:.0f} flop per queued test"},
                 "avg_launch_ms": avg_ms,
                 "hbm_vertex_stream_gbs": hbm_achieved, "hbm_peak_gbs": peaks.get("hbm_gbs"),

@@ -1272,6 +1272,10 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
 // ---------------------------------------------------------------------------
 struct CullBWarpSmem {
     float st[SETUP_FIELDS][32];  // field-major setups of the warp's 32 pairs
+    uint32_t meta[32];           // per pair: first channel | ray count << 10 | sensor << 26
+    uint32_t r0[32];             // per pair: first ray index (wrapped)
+    uint32_t tri[32];            // per pair: triangle id
+    float inv[32];               // per pair: rounded-up 1 / ray count
     uint32_t cnt[8];             // live, cand, inl, big, tests, hits, unc, ties
 };
 template <bool RECHECK, bool BRUTE>
@@ -1288,9 +1292,8 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
     const uint32_t gwarp = ((blockIdx.x * blockDim.x) >> 5) + wib;
     for (uint32_t b0 = gwarp * 32; b0 < n; b0 += n_warps * 32) {
         const uint32_t q = b0 + lane;
-        uint32_t ncand = 0, my_tri = 0, my_meta = 0, my_r0 = 0;
+        uint32_t ncand = 0;
         uint32_t l_live = 0, l_cand = 0, l_big = 0, hit0 = 0, tested0 = 0;
-        float my_inv = 0.f;
         if (q < n) {
             const unsigned long long r = __ldcs(&a.surv[q]);
             const uint32_t tri = (uint32_t)r, span = (uint32_t)(r >> 32) & 0x1FFFFFu, sn = (uint32_t)(r >> 53);
@@ -1379,10 +1382,11 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
                     bool det_unc = fabsf(det) <= err_det;
                     if (det != 0.f || (RECHECK && det_unc)) {
                         make_setup(S, T, w, p, det, err_det, SetupWriterSoA{&W.st[0][0], lane});
-                        my_tri = tri;
-                        my_meta = (uint32_t)sp.j_lo | ((uint32_t)sp.n_r << 10) | (sn << 26);
-                        my_r0 = (uint32_t)imod(sp.u_lo, (int)S.n_rays);
-                        my_inv = __frcp_ru((float)sp.n_r);
+                        const uint32_t my_r0 = (uint32_t)imod(sp.u_lo, (int)S.n_rays);
+                        W.tri[lane] = tri;
+                        W.meta[lane] = (uint32_t)sp.j_lo | ((uint32_t)sp.n_r << 10) | (sn << 26);
+                        W.r0[lane] = my_r0;
+                        W.inv[lane] = __frcp_ru((float)sp.n_r);
                         // the pair's first candidate is tested here by its own lane;
                         // the remaining ones are expanded cooperatively below
                         const uint32_t g = S.ray_off + (uint32_t)sp.j_lo * S.n_rays + my_r0;
@@ -1431,10 +1435,10 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
             const uint32_t rank = base_rank + __popc(starts & ((2u << lane) - 2u));
             const uint32_t own = __fns(nz, 0, (int)min(rank, 31u) + 1);
             const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, own & 31u);
-            const uint32_t meta = __shfl_sync(0xffffffffu, my_meta, own & 31u);
-            const uint32_t r0o = __shfl_sync(0xffffffffu, my_r0, own & 31u);
-            const uint32_t tri = __shfl_sync(0xffffffffu, my_tri, own & 31u);
-            const float inv = __shfl_sync(0xffffffffu, my_inv, own & 31u);
+            const uint32_t meta = W.meta[own & 31u];
+            const uint32_t r0o = W.r0[own & 31u];
+            const uint32_t tri = W.tri[own & 31u];
+            const float inv = W.inv[own & 31u];
             const uint32_t cc = c0 + lane;
             uint32_t hit = 0;
             if (cc < total) {
@@ -1869,6 +1873,7 @@ __global__ void __launch_bounds__(128, 4) k_bvh(CastArgs a) {
     uint32_t n_vis = 0, n_tst = 0, c_unc = 0, c_ties = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
     int32_t stack[BVH_STACK];
+    constexpr int32_t DONE = 0x7FFFFFFF;  // no inner node has this index (nodes < 2^27)
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_rays_total; g += stride) {
         uint32_t sn = 0;
         for (uint32_t k = 1; k < a.n_sensors; ++k)
@@ -1877,19 +1882,22 @@ __global__ void __launch_bounds__(128, 4) k_bvh(CastArgs a) {
         const uint32_t q = g - S.ray_off;
         const uint32_t j = q / S.n_rays, i = q - j * S.n_rays;
         const V3 d = ray_dir(__ldg(&a.ch_sc[S.ch_off + j]), __ldg(&a.az_sc[S.az_off + i]));
-        // world direction B^T d for the box tests (the triangle test uses d)
+        // world direction B^T d for the box tests and the leaf pre-test (the exact test uses d)
         const V3 dw = {S.B[0] * d.x + S.B[3] * d.y + S.B[6] * d.z, S.B[1] * d.x + S.B[4] * d.y + S.B[7] * d.z,
                        S.B[2] * d.x + S.B[5] * d.y + S.B[8] * d.z};
         const V3 inv = {1.f / (dw.x != 0.f ? dw.x : 1e-30f), 1.f / (dw.y != 0.f ? dw.y : 1e-30f),
                         1.f / (dw.z != 0.f ? dw.z : 1e-30f)};
         const V3 o = {S.o_hi[0], S.o_hi[1], S.o_hi[2]};
+        // pre-test margin term of the origin's low part (|o_lo| <= u |o|)
+        const float o_term = 2.f * U32 * (fabsf(o.x) + fabsf(o.y) + fabsf(o.z));
         unsigned long long cur = __ldcg(&a.keys[g]);
         const float tmin = fmaxf(S.d_min * (1.f - 2e-5f) - 2e-6f, 0.f);
         float tmax = fminf(S.d_max * (1.f + 2e-5f) + 2e-6f, __uint_as_float((uint32_t)(cur >> 32)) * (1.f + 4.f * BETA));
         int sp = 0;
         int32_t node = 0;
-        while (true) {
-            if (node >= 0) {
+        while (node != DONE) {
+            // inner nodes until a leaf is in hand (the warp then tests leaves together)
+            while (node >= 0 && node != DONE) {
                 const float4* np = reinterpret_cast<const float4*>(a.bvh_nodes + node);
                 const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2);
                 const int4 n3 = __ldg(reinterpret_cast<const int4*>(np) + 3);
@@ -1913,16 +1921,33 @@ __global__ void __launch_bounds__(128, 4) k_bvh(CastArgs a) {
                 } else if (h0 || h1) {
                     node = h0 ? n3.x : n3.y;
                 } else {
-                    if (sp == 0) break;
-                    node = stack[--sp];
+                    node = sp ? stack[--sp] : DONE;
                 }
-                continue;
             }
+            if (node == DONE) break;
             const uint32_t lf = ((uint32_t)node >> 3) & 0x0FFFFFFFu, cnt = ((uint32_t)node & 7u) + 1u;
             for (uint32_t k = lf; k < lf + cnt; ++k) {
                 float t9[9];
 #pragma unroll
                 for (int m = 0; m < 9; ++m) t9[m] = __ldg(a.bvh_tris + 9ull * k + m);
+                n_tst++;
+                {
+                    // world-frame pre-test: the edge functions F_k = dw.((v_k - o) x (v_k+1 - v_k))
+                    // follow the winding, so a ray inside has all three of one sign.  Skip
+                    // the triangle only if two have provably opposite signs; the margin
+                    // covers this evaluation's rounding, the FP32 direction and origin
+                    // differences and the exact test's own error bound, so nothing the
+                    // exact test could report as a hit or send to the re-test is skipped.
+                    const V3 v0 = {t9[0], t9[1], t9[2]}, v1 = {t9[3], t9[4], t9[5]}, v2 = {t9[6], t9[7], t9[8]};
+                    const V3 a0 = vsub(v0, o), a1 = vsub(v1, o), a2 = vsub(v2, o);
+                    const V3 e0 = vsub(v1, v0), e1 = vsub(v2, v1), e2 = vsub(v0, v2);
+                    const float F0 = vdot(dw, vcross(a0, e0)), F1 = vdot(dw, vcross(a1, e1)), F2 = vdot(dw, vcross(a2, e2));
+                    auto l1 = [](V3 x) { return fabsf(x.x) + fabsf(x.y) + fabsf(x.z); };
+                    const float m0 = (64.f * U32 * l1(a0) + o_term) * l1(e0), m1 = (64.f * U32 * l1(a1) + o_term) * l1(e1),
+                                m2 = (64.f * U32 * l1(a2) + o_term) * l1(e2);
+                    const bool neg = F0 < -m0 || F1 < -m1 || F2 < -m2, pos = F0 > m0 || F1 > m1 || F2 > m2;
+                    if (neg && pos) continue;
+                }
                 TriW T;
                 tri_world(t9, T);
                 if (T.n.x == 0.f && T.n.y == 0.f && T.n.z == 0.f) continue;  // zero area: never hit
@@ -1940,7 +1965,6 @@ __global__ void __launch_bounds__(128, 4) k_bvh(CastArgs a) {
                 make_setup(S, T, w, p, det, err_det, SetupWriterReg{sr});
                 float t, terr;
                 const int res = test_fp32<RECHECK>(sr, S, d, t, terr);
-                n_tst++;
                 if (res == T_MISS) continue;
                 const uint32_t tri = __ldg(a.bvh_prim + k);
                 commit_pre<RECHECK>(a, g, tri, res, t, terr, cur, c_unc, c_ties);
@@ -1950,8 +1974,7 @@ __global__ void __launch_bounds__(128, 4) k_bvh(CastArgs a) {
                     tmax = fminf(tmax, t * (1.f + 4.f * BETA));
                 }
             }
-            if (sp == 0) break;
-            node = stack[--sp];
+            node = sp ? stack[--sp] : DONE;
         }
     }
     n_vis = __reduce_add_sync(0xffffffffu, n_vis);
