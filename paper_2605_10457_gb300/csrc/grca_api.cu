@@ -83,6 +83,9 @@ struct grca_ctx {
     double bvh_delta = 0.0;
     float bvh_lo[3] = {0, 0, 0}, bvh_hi[3] = {0, 0, 0};
     uint32_t pending_launches = 0;  // group-bound kernels launched since the last cast
+    // triangles whose group boxes are stale: [gb_lo, gb_hi) (refreshed lazily,
+    // by the first cast that runs the group cull)
+    uint32_t gb_lo = 0, gb_hi = 0;
     uint32_t n_tris = 0;
     size_t tris_cap = 0;  // triangles
 
@@ -420,8 +423,8 @@ grca_status grca_upload_triangles(grca_ctx* ctx, const float* xyz, uint32_t n_tr
     if (ctx->n_static) ctx->bvh_stale = true;  // a new triangle set: rebuild the static hierarchy to use it
     grca_status rs = copy_in(ctx, ctx->d_tris, xyz, 9ull * n_tris, where, st);
     if (rs != GRCA_OK) return rs;
-    launch_group_bounds(ctx->d_tris, n_tris, 0, n_tris, ctx->d_gb, ctx->n_sm, st);
-    if (n_tris) ctx->pending_launches++;
+    ctx->gb_lo = 0;
+    ctx->gb_hi = n_tris;
     CK(cudaGetLastError());
     return GRCA_OK;
 }
@@ -434,8 +437,15 @@ grca_status grca_update_vertices(grca_ctx* ctx, const float* xyz, uint32_t first
     if (n_tris && first < ctx->n_static) ctx->bvh_stale = true;  // static triangles moved
     grca_status rs = copy_in(ctx, ctx->d_tris + 9ull * first, xyz, 9ull * n_tris, where, (cudaStream_t)stream);
     if (rs != GRCA_OK) return rs;
-    launch_group_bounds(ctx->d_tris, ctx->n_tris, first, n_tris, ctx->d_gb, ctx->n_sm, (cudaStream_t)stream);
-    if (n_tris) ctx->pending_launches++;
+    if (n_tris) {
+        if (ctx->gb_hi <= ctx->gb_lo) {
+            ctx->gb_lo = first;
+            ctx->gb_hi = first + n_tris;
+        } else {
+            ctx->gb_lo = std::min(ctx->gb_lo, first);
+            ctx->gb_hi = std::max(ctx->gb_hi, first + n_tris);
+        }
+    }
     CK(cudaGetLastError());
     return GRCA_OK;
 }
@@ -760,6 +770,13 @@ static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, f
     bool finite_range = false;
     for (uint32_t k = 0; k < n; ++k) finite_range |= std::isfinite(ctx->sensors[ids[k]].d.d_max);
     a.gbounds = (flags & GRCA_CAST_NO_GROUP_CULL) || !finite_range ? nullptr : ctx->d_gb;
+    if (a.gbounds && ctx->gb_hi > ctx->gb_lo) {
+        // refresh the boxes of the groups touched since the last refresh (stream-ordered before the cast)
+        launch_group_bounds(ctx->d_tris, ctx->n_tris, ctx->gb_lo, ctx->gb_hi - ctx->gb_lo, ctx->d_gb, ctx->n_sm, st);
+        CK(cudaGetLastError());
+        ctx->pending_launches++;
+        ctx->gb_lo = ctx->gb_hi = 0;
+    }
     // hybrid: static triangles through the hierarchy when it is current, the
     // mode allows it and every sensor is close enough for its box inflation
     bool hybrid = ctx->d_bvh_nodes && !ctx->bvh_stale && ctx->n_static &&

@@ -230,7 +230,10 @@ __device__ __forceinline__ int test_fp32(const SV& st, const SensorDev& S, V3 d,
     V3 m0 = {st.f(0), st.f(1), st.f(2)}, m1 = {st.f(3), st.f(4), st.f(5)}, m2 = {st.f(6), st.f(7), st.f(8)};
     float E0 = vdot(d, m0), E1 = vdot(d, m1), E2 = vdot(d, m2);
     float dn = vdot(d, {st.f(12), st.f(13), st.f(14)});
-    t = __fdiv_rn(st.f(15), dn);
+    // t = det / dn through one correctly rounded reciprocal (also used by the
+    // error bound); t then carries <= 1 ulp more error than a division
+    const float rdn = __frcp_rn(dn);
+    t = __fmul_rn(st.f(15), rdn);
     t_err = 0.f;
     if (!RECHECK) {
         if (E0 < 0.f || E1 < 0.f || E2 < 0.f) return T_MISS;
@@ -249,8 +252,7 @@ __device__ __forceinline__ int test_fp32(const SV& st, const SensorDev& S, V3 d,
         return T_MISS;
     }
     bool inside = E0 > tau0 && E1 > tau1 && E2 > tau2;
-    float adn = fabsf(dn);
-    t_err = st.f(16) + (fabsf(d.x) * st.f(18) + fabsf(d.y) * st.f(19) + fabsf(d.z) * st.f(20)) / adn;
+    t_err = st.f(16) + (fabsf(d.x) * st.f(18) + fabsf(d.y) * st.f(19) + fabsf(d.z) * st.f(20)) * fabsf(rdn) + 2.4e-7f;
     if (!(t > 0.f) || !(t_err < 0.25f)) {
         t_err = 1.f;
         return (inside && !unc_pair && !(t > 0.f)) ? T_MISS : T_UNCERTAIN;
@@ -461,15 +463,19 @@ __device__ __forceinline__ float az_pad(V3 p) {
     return h2 > 1e-12f * r2 ? 16.f * U32 * sqrtf(r2 / h2) : 10.f;
 }
 
+__device__ __forceinline__ float fast_atan2(float y, float x);
+
 // angle from a to b in the xy plane, in (-pi, pi]; small angles by the
-// series atan(x) = x - x^3/3 + x^5/5 (error < x^7/7 < 2e-12 for |x| < 0.02)
+// series atan(x) = x - x^3/3 + x^5/5 (error < x^7/7 < 2e-12 for |x| < 0.02),
+// larger ones by fast_atan2 (error < FAST_ATAN_PAD)
 __device__ __forceinline__ float rel_angle(V3 a, V3 b) {
     float cr = cross2(a, b), dt = dot2(a, b);
     if (dt > 0.f && fabsf(cr) < 0.02f * dt) {
-        float x = cr / dt, x2 = x * x;
+        // |x| < 0.02; the fast division's 2-ulp error adds < 1e-8 rad
+        float x = __fdividef(cr, dt), x2 = x * x;
         return x * (1.f - x2 * (0.33333334f - 0.2f * x2));
     }
-    return atan2f(cr, dt);
+    return fast_atan2(cr, dt);  // callers pad by FAST_ATAN_PAD per call
 }
 
 // Does the vertical axis through the origin meet the triangle?  Point in the
@@ -602,8 +608,9 @@ __device__ __forceinline__ bool elev_range_w(const SensorDev& S, const V3 w[3], 
         float m2 = fminf(r2[k], r2[k1]);
         float ee = 1.0001f * eeT[k] + 5.7e-10f * fmaxf(r2[k], r2[k1]);
         ee_max = fmaxf(ee_max, ee);
-        if (ee < 1e-5f * m2) {
-            dev = fmaxf(dev, 0.31f * ee * __frcp_ru(m2));
+        if (ee < 1e-5f * m2 && m2 > 1e-30f && m2 < 1e36f) {
+            // 0.31 ee / m2 with the fast division (2 ulp) rounded up by the constant
+            dev = fmaxf(dev, 0.3100004f * __fdividef(ee, m2));
         } else {
             V3 e = {w[k1].x - a.x, w[k1].y - a.y, w[k1].z - a.z};
             ee = e.x * e.x + e.y * e.y + e.z * e.z;
@@ -739,8 +746,8 @@ __device__ __forceinline__ uint32_t pack_span(int jl, int jh, bool pierced) {
 // the channel span from the elevation range.  Returns false when culled.
 template <bool RECHECK, bool BRUTE, typename T>
 __device__ __forceinline__ bool cull_elevation(const SensorDev& S, const T* ch, const uint16_t* lut, const V3 v[3],
-                                               const V3& nw, const float eeT[3], bool cull_back, bool lossy_area,
-                                               float area_eps2, uint32_t& span) {
+                                               const V3& nw, const float eeT[3], float lmax, bool cull_back,
+                                               bool lossy_area, float area_eps2, uint32_t& span) {
     V3 w0 = rel_origin(S, v[0]);
     if (cull_back) {
         float det = vdot(w0, nw);
@@ -755,15 +762,13 @@ __device__ __forceinline__ bool cull_elevation(const SensorDev& S, const T* ch, 
     }
     const V3 wv[3] = {w0, rel_origin(S, v[1]), rel_origin(S, v[2])};
     if (S.d_max < INFINITY) {
-        // range pre-cull (App. A.4.1 Step 1), only where provably empty: the
-        // farthest vertex inside d_min, or every point beyond d_max (each point
-        // lies within the longest edge of every vertex); skipped for unlimited
-        // range, where a d_min of centimetres would almost never drop a pair
-        const float r0 = vdot(wv[0], wv[0]), r1 = vdot(wv[1], wv[1]), r2 = vdot(wv[2], wv[2]);
-        const float dlo = fmaxf(S.d_min * (1.f - 2e-5f) - 2e-6f, 0.f);
-        if (fmaxf(r0, fmaxf(r1, r2)) < dlo * dlo) return false;
-        const float near = sqrtf(fminf(r0, fminf(r1, r2))) - sqrtf(fmaxf(eeT[0], fmaxf(eeT[1], eeT[2])));
-        if (near > S.d_max * (1.f + 2e-5f) + 2e-6f) return false;  // false for d_max = +inf
+        // range pre-cull (App. A.4.1 Step 1), only where provably empty: every
+        // point of the triangle lies within lmax (the longest edge) of vertex 0,
+        // so its distance is within |w0| -+ lmax; skipped for unlimited range,
+        // where a d_min of centimetres would almost never drop a pair
+        const float d0 = sqrtf(vdot(wv[0], wv[0]));
+        if (d0 - lmax > S.d_max * (1.f + 2e-5f) + 2e-6f) return false;
+        if (d0 + lmax < S.d_min * (1.f - 2e-5f) - 2e-6f) return false;
     }
     if (lossy_area) {
         // Eq. apparent_area: A_T (c-o).n^ = (c-o).n / 2 with n = (v1-v0)x(v2-v0)
@@ -819,7 +824,7 @@ __device__ __forceinline__ void cull_rest(const CastArgs& a, const SensorDev& S,
         } else {
             float d1 = rel_angle(p[0], p[1]);
             float d2 = rel_angle(p[0], p[2]);
-            float pad = EPS_T + FAST_ATAN_PAD + az_pad2(p[0]) + az_pad2(p[1]) + az_pad2(p[2]);
+            float pad = EPS_T + 3.f * FAST_ATAN_PAD + az_pad2(p[0]) + az_pad2(p[1]) + az_pad2(p[2]);
             float lo = fminf(0.f, fminf(d1, d2)) - pad, hi = fmaxf(0.f, fmaxf(d1, d2)) + pad;
             if (hi - lo >= 6.2831f) {
                 A = sp.a0 - 0.5f * S.period;
@@ -959,6 +964,8 @@ __global__ void __launch_bounds__(256, 3) k_cull(CastArgs a) {
             V3 e = vsub(v[k == 2 ? 0 : k + 1], v[k]);
             eeT[k] = vdot(e, e);
         }
+        // longest edge, rounded up (sensor independent)
+        const float lmax = sqrtf(fmaxf(eeT[0], fmaxf(eeT[1], eeT[2]))) * (1.f + 1e-6f);
         for (uint32_t sg = 0; sg < a.n_sensors; sg += CULL_GROUP) {
             const uint32_t ng = min((uint32_t)CULL_GROUP, a.n_sensors - sg);
             uint32_t mask = 0;
@@ -966,7 +973,7 @@ __global__ void __launch_bounds__(256, 3) k_cull(CastArgs a) {
                 for (uint32_t k = 0; k < ng; ++k) {
                     uint32_t span;
                     if (cull_elevation<RECHECK, BRUTE>(M.sens[sg + k], M.ch + M.sens[sg + k].ch_loc,
-                                                       M.lut + (sg + k) * LUT_BINS, v, nw, eeT, cull_back,
+                                                       M.lut + (sg + k) * LUT_BINS, v, nw, eeT, lmax, cull_back,
                                                        (a.flags & 32u) != 0, a.area_eps2, span)) {
                         mask |= 1u << k;
                         W.span[lane * CULL_GROUP + k] = span;
@@ -1239,6 +1246,8 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
             V3 e = vsub(v[k == 2 ? 0 : k + 1], v[k]);
             eeT[k] = vdot(e, e);
         }
+        // longest edge, rounded up (sensor independent)
+        const float lmax = sqrtf(fmaxf(eeT[0], fmaxf(eeT[1], eeT[2]))) * (1.f + 1e-6f);
         for (uint32_t sg = 0; sg < a.n_sensors; sg += CULL_A_GROUP) {
             const uint32_t ng = min((uint32_t)CULL_A_GROUP, a.n_sensors - sg);
             if (fill + 32 * CULL_A_GROUP > SURV_BUF) flush_survivors(a, W, fill, lane, a.n_sensors);
@@ -1247,7 +1256,8 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
                 uint32_t span = 0;
                 const SensorDev& S = M.sens[sg + k];
                 bool ok = valid && cull_elevation<RECHECK, BRUTE>(S, M.sins + S.ch_loc, M.lut + (sg + k) * LUT_BINS, v,
-                                                                  nw, eeT, cull_back, lossy_area, a.area_eps2, span);
+                                                                  nw, eeT, lmax, cull_back, lossy_area, a.area_eps2,
+                                                                  span);
                 uint32_t bal = __ballot_sync(0xffffffffu, ok);
                 if (ok)
                     W.buf[fill + __popc(bal & ((1u << lane) - 1u))] =
@@ -1276,6 +1286,7 @@ struct CullBWarpSmem {
     uint32_t r0[32];             // per pair: first ray index (wrapped)
     uint32_t tri[32];            // per pair: triangle id
     float inv[32];               // per pair: rounded-up 1 / ray count
+    uint32_t own[32];            // lane of the pair with the r-th candidate run (r-th set bit of the owner mask)
     uint32_t cnt[8];             // live, cand, inl, big, tests, hits, unc, ties
 };
 template <bool RECHECK, bool BRUTE>
@@ -1286,7 +1297,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
     CullBWarpSmem& W = reinterpret_cast<CullBWarpSmem*>(M.rest)[wib];
     const bool dump = a.flags & 16u;
     if (lane < 8) W.cnt[lane] = 0;
-    uint32_t c_unc = 0, c_ties = 0;
+    uint32_t c_unc = 0, c_ties = 0, c_hits = 0;
     const uint32_t n = min(*(volatile uint32_t*)&a.qcount[Q_SURV], a.surv_cap);
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t gwarp = ((blockIdx.x * blockDim.x) >> 5) + wib;
@@ -1315,7 +1326,9 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
                 float dmax2 = fmaxf(vdot(w[0], w[0]), fmaxf(vdot(w[1], w[1]), vdot(w[2], w[2])));
                 float dlo = fmaxf(S.d_min * (1.f - 1e-5f) - 1e-6f, 0.f);
                 if (dmax2 < dlo * dlo) keep = false;
-                if (keep && S.d_max < INFINITY && closest_dist(w[0], w[1], w[2]) > S.d_max * (1.f + 1e-5f) + 1e-6f)
+                const float dhi = S.d_max * (1.f + 1e-5f) + 1e-6f;
+                // the closest point matters only if some vertex lies beyond d_max
+                if (keep && S.d_max < INFINITY && dmax2 > dhi * dhi && closest_dist(w[0], w[1], w[2]) > dhi)
                     keep = false;
             }
             Span sp;
@@ -1336,7 +1349,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
                     } else {
                         float d1 = rel_angle(p[0], p[1]);
                         float d2 = rel_angle(p[0], p[2]);
-                        float pad = EPS_T + FAST_ATAN_PAD + az_pad2(p[0]) + az_pad2(p[1]) + az_pad2(p[2]);
+                        float pad = EPS_T + 3.f * FAST_ATAN_PAD + az_pad2(p[0]) + az_pad2(p[1]) + az_pad2(p[2]);
                         float lo = fminf(0.f, fminf(d1, d2)) - pad, hi = fmaxf(0.f, fmaxf(d1, d2)) + pad;
                         if (hi - lo >= 6.2831f) {
                             A = sp.a0 - 0.5f * S.period;
@@ -1412,6 +1425,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
         const uint32_t excl = incl - ncand;
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         const uint32_t nz = __ballot_sync(0xffffffffu, ncand > 0);   // lanes that own candidates, in order
+        if (ncand > 0) W.own[__popc(nz & ((1u << lane) - 1u))] = lane;
         {
             const uint32_t s_live = __reduce_add_sync(0xffffffffu, l_live), s_cand = __reduce_add_sync(0xffffffffu, l_cand),
                            s_big = __reduce_add_sync(0xffffffffu, l_big), s_t0 = __reduce_add_sync(0xffffffffu, tested0),
@@ -1433,14 +1447,13 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
             const uint32_t starts =
                 __reduce_or_sync(0xffffffffu, (ncand > 0 && excl > c0 && excl < c0 + 32) ? (1u << (excl - c0)) : 0u);
             const uint32_t rank = base_rank + __popc(starts & ((2u << lane) - 2u));
-            const uint32_t own = __fns(nz, 0, (int)min(rank, 31u) + 1);
+            const uint32_t own = W.own[min(rank, 31u)];
             const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, own & 31u);
             const uint32_t meta = W.meta[own & 31u];
             const uint32_t r0o = W.r0[own & 31u];
             const uint32_t tri = W.tri[own & 31u];
             const float inv = W.inv[own & 31u];
             const uint32_t cc = c0 + lane;
-            uint32_t hit = 0;
             if (cc < total) {
                 const uint32_t nr = (meta >> 10) & 0xFFFFu;
                 const uint32_t sn = meta >> 26;
@@ -1464,18 +1477,18 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
                 float t, terr;
                 int res = test_fp32<RECHECK>(SetupSoA{&W.st[0][0], own & 31u}, S, d, t, terr);
                 if (dump) dump_candidate(a, g, tri);
-                hit = commit_pre<RECHECK>(a, g, tri, res, t, terr, cur, c_unc, c_ties);
+                c_hits += commit_pre<RECHECK>(a, g, tri, res, t, terr, cur, c_unc, c_ties);
             }
-            const uint32_t s_hits = __reduce_add_sync(0xffffffffu, hit);
-            if (lane == 0) W.cnt[5] += s_hits;
         }
         __syncwarp();
     }
     c_unc = __reduce_add_sync(0xffffffffu, c_unc);
     c_ties = __reduce_add_sync(0xffffffffu, c_ties);
+    c_hits = __reduce_add_sync(0xffffffffu, c_hits);
     __syncwarp();
     if (lane == 0) {
         const int idx[8] = {C_PAIRS_LIVE, C_CAND, C_CAND_INLINE, C_BIG, C_TESTS, C_HITS, C_UNCERTAIN, C_TIES};
+        W.cnt[5] += c_hits;
         W.cnt[6] = c_unc;
         W.cnt[7] = c_ties;
 #pragma unroll
@@ -1500,7 +1513,7 @@ __device__ __forceinline__ bool channel_span_rel(const V3 p[3], const float s_v[
     V3 p0 = p[0];
     auto include = [&](V3 q, float extra) {
         float ang = rel_angle(p0, q);
-        float pad = EPS_ROW + az_pad(q) + extra;
+        float pad = EPS_ROW + FAST_ATAN_PAD + az_pad(q) + extra;
         lo = fminf(lo, ang - pad);
         hi = fmaxf(hi, ang + pad);
         any = true;

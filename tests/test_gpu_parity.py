@@ -276,6 +276,35 @@ def test_edge_cases():
     assert g["errors"] == 0, g
 
 
+def test_sixty_four_sensors_in_one_cast():
+    """The largest batch one cast takes (64 sensors), of mixed grids, poses,
+    fields of view and ranges, every ray against the oracle."""
+    from paper_2605_10457_gb300.grca import CAST_FP64_RECHECK, CAST_GRAPH
+    rng = np.random.default_rng(64)
+    sens = []
+    for k in range(64):
+        n_ch = int(rng.choice([2, 4, 8]))
+        elev = np.sort(rng.uniform(-0.4, 0.3, n_ch))
+        fov = float(rng.choice([360.0, 180.0, 90.0]))
+        d_max = float(rng.choice([np.inf, 8.0, 3.0]))
+        sens.append(make_sensor(rng.uniform(-3, 3, 3) * [1, 1, 0.2] + [0, 0, 1], yaw=float(rng.uniform(-3, 3)),
+                                elev=elev, n_rays=int(rng.choice([32, 64, 96])), fov_deg=fov,
+                                d_min=float(rng.choice([0.0, 0.5])), d_max=d_max,
+                                pitch=float(rng.uniform(-0.2, 0.2))))
+    tris = tiny_scene(64, n_tris=600, extent=8.0)
+    c = _caster()
+    ids = [c.add_sensor(s) for s in sens]
+    c.upload(tris)
+    d, t = _cast(c, ids, CAST_FP64_RECHECK | CAST_GRAPH)
+    assert c.stats()["device_error"] == 0
+    S = type("S", (), {"sensors": sens})
+    g = _check(S, tris, d, t)
+    assert g["errors"] == 0, g
+    assert g["hits"] > 1000
+    with pytest.raises(Exception):
+        c.cast(ids + [ids[0]], CAST_FP64_RECHECK)        # 65 sensors: rejected
+
+
 def test_capacity_overflow_is_reported():
     from paper_2605_10457_gb300.grca import CAST_FP64_RECHECK
     sc = scene_c1()
