@@ -189,9 +189,14 @@ grca_status grca_cast(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_senso
                       uint32_t* out_tri, uint32_t flags, void* stream);
 
 /* Same as grca_cast with HOST output arrays: the frame's vertices
- * (`xyz_dynamic`, n_dynamic triangles starting at first_dynamic, HOST) are
- * copied in first, the results copied back into the host arrays, and the
- * call returns once they are there (end-to-end frame). */
+ * (`xyz_dynamic`, n_dynamic triangles starting at first_dynamic, HOST;
+ * pinned memory gives the fastest copy) are copied in, the results copied
+ * back into the host arrays, and the call returns once they are there
+ * (end-to-end frame).  When the dynamic triangles are the tail of the set
+ * (first_dynamic + n_dynamic = uploaded count, first_dynamic > 0), their copy
+ * runs on an internal stream while the elevation cull works through the
+ * triangles before them.  Returns GRCA_ERR_INVALID_ARG for a range outside
+ * the uploaded set. */
 grca_status grca_cast_host(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_sensors, const float* xyz_dynamic,
                            uint32_t first_dynamic, uint32_t n_dynamic, float* out_dist_host,
                            uint32_t* out_tri_host, uint32_t flags, void* stream);

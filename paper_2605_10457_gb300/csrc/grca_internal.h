@@ -180,8 +180,16 @@ struct KernelMarks {
 };
 
 // launcher (grca_kernels.cu); returns the number of kernels launched
+// A frame may be launched in two parts around a wait on the host-to-device
+// copy of its dynamic triangles [at, n_tris): part 1 = key init + the
+// elevation cull of [tri_first, at); part 2 = the elevation cull of
+// [at, n_tris) and everything after it.  part 0 = the whole frame.
+struct FrameSplit {
+    int part = 0;
+    uint32_t at = 0;
+};
 int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t st,
-                 const KernelMarks* marks = nullptr);
+                 const KernelMarks* marks = nullptr, FrameSplit split = FrameSplit());
 size_t cull_smem_bytes(const CastArgs& a, const LaunchCfg& cfg);  // fused k_cull
 
 // ---------------------------------------------------------------------------

@@ -132,6 +132,19 @@ struct SetupWriterSoA {
     __device__ __forceinline__ void set(int k, float v) { base[k * 32 + i] = v; }
 };
 
+// upper bounds for error-bound arithmetic: hardware approximations (relative
+// error <= 2^-22) scaled up by 1 + 2^-18.9
+__device__ __forceinline__ float sqrt_up(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r * 1.000002f;
+}
+__device__ __forceinline__ float rcp_up(float x) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r * 1.000002f;
+}
+
 template <typename WR>
 __device__ __forceinline__ void make_setup(const SensorDev& S, const TriW& T, const V3 w[3], const V3 p[3], float det,
                                            float err_det_abs, WR out) {
@@ -158,14 +171,14 @@ __device__ __forceinline__ void make_setup(const SensorDev& S, const TriW& T, co
         // FP32 error bound of d.m: errors of p_base, e (rotation, origin) and of
         // the cross and dot products, all <= 18 u |p_base| |e| (|m| <= |p_base| |e|)
         float ee = T.E[k].x * T.E[k].x + T.E[k].y * T.E[k].y + T.E[k].z * T.E[k].z;
-        out.set(9 + k, 18.f * U32 * sqrtf(rb * ee) + 1e-30f);
+        out.set(9 + k, 18.f * U32 * sqrt_up(rb * ee) + 1e-30f);
     }
     V3 ne = rotB(S.B, T.n);
     out.set(12, ne.x);
     out.set(13, ne.y);
     out.set(14, ne.z);
     out.set(15, det);
-    out.set(16, det != 0.f ? err_det_abs / fabsf(det) : 1.f);
+    out.set(16, det != 0.f ? err_det_abs * rcp_up(fabsf(det)) : 1.f);
     out.set(17, __uint_as_float(unc ? 1u : 0u));
     float q0 = 3.f * (fabsf(T.n.x) + T.N.x), q1 = 3.f * (fabsf(T.n.y) + T.N.y), q2 = 3.f * (fabsf(T.n.z) + T.N.z);
     out.set(18, U32 * (fabsf(S.B[0]) * q0 + fabsf(S.B[1]) * q1 + fabsf(S.B[2]) * q2 + 6.f * fabsf(ne.x)));
@@ -608,8 +621,9 @@ __device__ __forceinline__ bool elev_range_w(const SensorDev& S, const V3 w[3], 
         float m2 = fminf(r2[k], r2[k1]);
         float ee = 1.0001f * eeT[k] + 5.7e-10f * fmaxf(r2[k], r2[k1]);
         ee_max = fmaxf(ee_max, ee);
-        if (ee < 1e-5f * m2 && m2 > 1e-30f && m2 < 1e36f) {
-            // 0.31 ee / m2 with the fast division (2 ulp) rounded up by the constant
+        if (ee < 1e-4f * m2 && m2 > 1e-30f && m2 < 1e36f) {
+            // 0.31 ee / m2 with the fast division (2 ulp) rounded up by the constant;
+            // alpha <= 0.016 rad here, where the arc's rise stays below 0.3085 ee / m2
             dev = fmaxf(dev, 0.3100004f * __fdividef(ee, m2));
         } else {
             V3 e = {w[k1].x - a.x, w[k1].y - a.y, w[k1].z - a.z};
@@ -2029,48 +2043,66 @@ const char* const kKernelNames[K_NUM] = {"k_init",  "k_cull_a",         "k_cull_
                                          "k_test",  "k_bvh",            "k_recheck_filter", "k_recheck_rays",
                                          "k_recheck_pairs", "k_decode"};
 
+// elevation cull of triangles [a.tri_first, a.n_tris) (ac) and/or the
+// survivor pass of the whole cast (a)
 template <bool R, bool B>
-static void launch_cull_split(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t st,
-                              const std::function<void(int, int)>& mark) {
-    size_t sa = cull_a_smem_bytes(a, cfg), sb = cull_b_smem_bytes(a);
-    const bool groups = !B && a.gbounds != nullptr;
-    ensure_smem_attr(k_cull_a<R, B, false>, sa);
-    if (groups) ensure_smem_attr(k_cull_a<R, B, true>, sa);
-    ensure_smem_attr(k_cull_b<R, B>, sb);
-    uint32_t max_blocks = (a.n_tris - (a.tri_first & ~31u) + cfg.cull_block - 1) / cfg.cull_block;
-    int grid_a = (int)std::min<uint32_t>(std::max<uint32_t>(max_blocks, 1u), (uint32_t)(n_sm * cfg.cull_blocks_per_sm));
-    mark(K_CULL_A, 0);
-    if (groups)
-        k_cull_a<R, B, true><<<grid_a, cfg.cull_block, sa, st>>>(a);
-    else
-        k_cull_a<R, B, false><<<grid_a, cfg.cull_block, sa, st>>>(a);
-    mark(K_CULL_A, 1);
-    mark(K_CULL_B, 0);
-    k_cull_b<R, B><<<n_sm * cfg.cull_blocks_per_sm * 2, 256, sb, st>>>(a);
-    mark(K_CULL_B, 1);
+static void launch_cull_split(const CastArgs& a, const CastArgs& ac, bool do_a, bool do_b, const LaunchCfg& cfg,
+                              int n_sm, cudaStream_t st, const std::function<void(int, int)>& mark) {
+    if (do_a) {
+        const size_t sa = cull_a_smem_bytes(ac, cfg);
+        const bool groups = !B && ac.gbounds != nullptr;
+        ensure_smem_attr(k_cull_a<R, B, false>, sa);
+        if (groups) ensure_smem_attr(k_cull_a<R, B, true>, sa);
+        const uint32_t span = ac.n_tris > (ac.tri_first & ~31u) ? ac.n_tris - (ac.tri_first & ~31u) : 0u;
+        const uint32_t max_blocks = (span + cfg.cull_block - 1) / cfg.cull_block;
+        const int grid_a =
+            (int)std::min<uint32_t>(std::max<uint32_t>(max_blocks, 1u), (uint32_t)(n_sm * cfg.cull_blocks_per_sm));
+        mark(K_CULL_A, 0);
+        if (groups)
+            k_cull_a<R, B, true><<<grid_a, cfg.cull_block, sa, st>>>(ac);
+        else
+            k_cull_a<R, B, false><<<grid_a, cfg.cull_block, sa, st>>>(ac);
+        mark(K_CULL_A, 1);
+    }
+    if (do_b) {
+        const size_t sb = cull_b_smem_bytes(a);
+        ensure_smem_attr(k_cull_b<R, B>, sb);
+        mark(K_CULL_B, 0);
+        k_cull_b<R, B><<<n_sm * cfg.cull_blocks_per_sm * 2, 256, sb, st>>>(a);
+        mark(K_CULL_B, 1);
+    }
 }
 
-int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t st, const KernelMarks* marks) {
+int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t st, const KernelMarks* marks,
+                 FrameSplit split) {
     const bool recheck = a.flags & 1u;
     const bool brute = a.flags & 4u;
     int launches = 0;
     std::function<void(int, int)> mark = [&](int k, int phase) {
         if (marks && marks->fn) marks->fn(marks->user, k, phase, st);
     };
-    int init_blocks = (int)std::min<uint32_t>((a.n_rays_total + 255) / 256, (uint32_t)n_sm * 8);
-    mark(K_INIT, 0);
-    k_init<<<max(init_blocks, 1), 256, 0, st>>>(a);
-    mark(K_INIT, 1);
-    launches++;
+    // the triangle range of this part's elevation cull
+    CastArgs ac = a;
+    if (split.part == 1) ac.n_tris = std::max(std::min(split.at, a.n_tris), a.tri_first);
+    if (split.part == 2) ac.tri_first = std::max(split.at, a.tri_first);
+    if (split.part != 2) {
+        int init_blocks = (int)std::min<uint32_t>((a.n_rays_total + 255) / 256, (uint32_t)n_sm * 8);
+        mark(K_INIT, 0);
+        k_init<<<max(init_blocks, 1), 256, 0, st>>>(a);
+        mark(K_INIT, 1);
+        launches++;
+    }
+    const bool do_b = split.part != 1;
     if (recheck && brute)
-        launch_cull_split<true, true>(a, cfg, n_sm, st, mark);
+        launch_cull_split<true, true>(a, ac, true, do_b, cfg, n_sm, st, mark);
     else if (recheck)
-        launch_cull_split<true, false>(a, cfg, n_sm, st, mark);
+        launch_cull_split<true, false>(a, ac, true, do_b, cfg, n_sm, st, mark);
     else if (brute)
-        launch_cull_split<false, true>(a, cfg, n_sm, st, mark);
+        launch_cull_split<false, true>(a, ac, true, do_b, cfg, n_sm, st, mark);
     else
-        launch_cull_split<false, false>(a, cfg, n_sm, st, mark);
-    launches += 2;
+        launch_cull_split<false, false>(a, ac, true, do_b, cfg, n_sm, st, mark);
+    launches += do_b ? 2 : 1;
+    if (split.part == 1) return launches;
     if (!brute) {
         mark(K_EXPAND, 0);
         k_expand<<<n_sm * 8, 256, 0, st>>>(a);
