@@ -144,8 +144,8 @@ typedef struct {
     uint64_t flagged_rays;    /* rays resolved by the FP64 re-test */
     uint64_t recheck_pairs;   /* queued (ray, triangle) pairs kept by the filter and re-tested in FP64 */
     uint64_t group_culled;    /* pairs skipped whole by the group-level cull (GACP-T_g) */
-    uint64_t bvh_node_visits; /* static-hierarchy nodes visited (hybrid casts) */
-    uint64_t bvh_tests;       /* ray-triangle tests on static leaves (hybrid casts) */
+    uint64_t bvh_node_visits; /* static-hierarchy node visits, one per warp of 32 rays (hybrid casts) */
+    uint64_t bvh_tests;       /* ray-triangle pre-tests on static leaves (hybrid casts) */
     uint64_t n_rays;          /* rays in the last cast */
     uint32_t device_error;    /* bit mask of device-side errors (0 = none) */
     uint32_t reserved;

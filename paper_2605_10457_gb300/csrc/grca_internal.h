@@ -20,7 +20,7 @@ constexpr int MAX_CHANNELS = 1024;
 constexpr int MAX_RAYS = 32768;
 
 // queue counters (device uint32[8])
-enum { Q_BIG = 0, Q_CHUNK = 1, Q_RECHECK = 2, Q_FLAG = 3, Q_DUMP = 4, Q_SURV = 5, Q_NUM = 8 };
+enum { Q_BIG = 0, Q_CHUNK = 1, Q_RECHECK = 2, Q_FLAG = 3, Q_DUMP = 4, Q_SURV = 5, Q_SURV_SPLIT = 6, Q_NUM = 8 };
 // statistics counters (device u64[16])
 enum {
     C_PAIRS = 0, C_PAIRS_LIVE, C_CAND, C_CAND_INLINE, C_BIG, C_CHUNKS, C_TESTS, C_HITS,
@@ -155,6 +155,9 @@ struct CastArgs {
     const struct BvhNode* bvh_nodes;  // nullptr: no static hierarchy in this cast
     const uint32_t* bvh_prim;         // leaf order -> triangle id
     const float* bvh_tris;            // vertices in leaf order (9 floats each)
+    // survivor pass over part of the queue: 0 all; 1 the survivors queued so
+    // far (and record their count); 2 the survivors queued after that
+    uint32_t surv_part;
 };
 
 struct LaunchCfg {
@@ -181,9 +184,10 @@ struct KernelMarks {
 
 // launcher (grca_kernels.cu); returns the number of kernels launched
 // A frame may be launched in two parts around a wait on the host-to-device
-// copy of its dynamic triangles [at, n_tris): part 1 = key init + the
-// elevation cull of [tri_first, at); part 2 = the elevation cull of
-// [at, n_tris) and everything after it.  part 0 = the whole frame.
+// copy of its dynamic triangles [at, n_tris): part 1 = key init, the
+// elevation cull of [tri_first, at) and the survivor pass over its
+// survivors; part 2 = the elevation cull of [at, n_tris), the survivor pass
+// over the survivors it adds, and everything after.  part 0 = the whole frame.
 struct FrameSplit {
     int part = 0;
     uint32_t at = 0;

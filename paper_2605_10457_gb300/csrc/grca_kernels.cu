@@ -137,12 +137,12 @@ struct SetupWriterSoA {
 __device__ __forceinline__ float sqrt_up(float x) {
     float r;
     asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r * 1.000002f;
+    return __fmul_rn(r, 1.000002f);
 }
 __device__ __forceinline__ float rcp_up(float x) {
     float r;
     asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r * 1.000002f;
+    return __fmul_rn(r, 1.000002f);
 }
 
 template <typename WR>
@@ -152,9 +152,12 @@ __device__ __forceinline__ void make_setup(const SensorDev& S, const TriW& T, co
     // forward hit <=> every emitter-frame edge function has the sign of the
     // emitter-frame triple product p0.(p1 x p2) = det(B) * det
     float fold = (det < 0.f ? -1.f : 1.f) * S.hand;
+    // every quantity that decides a test outcome is computed with explicitly
+    // rounded operations, so that all kernels that set up a pair (culled,
+    // deferred and hierarchy paths) get the same bits
     float r2[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) r2[k] = w[k].x * w[k].x + w[k].y * w[k].y + w[k].z * w[k].z;
+    for (int k = 0; k < 3; ++k) r2[k] = vdot(w[k], w[k]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         V3 e = rotB(S.B, T.E[k]);
@@ -170,32 +173,37 @@ __device__ __forceinline__ void make_setup(const SensorDev& S, const TriW& T, co
         out.set(3 * k + 2, m.z);
         // FP32 error bound of d.m: errors of p_base, e (rotation, origin) and of
         // the cross and dot products, all <= 18 u |p_base| |e| (|m| <= |p_base| |e|)
-        float ee = T.E[k].x * T.E[k].x + T.E[k].y * T.E[k].y + T.E[k].z * T.E[k].z;
-        out.set(9 + k, 18.f * U32 * sqrt_up(rb * ee) + 1e-30f);
+        const float ee = vdot(T.E[k], T.E[k]);
+        out.set(9 + k, __fmaf_rn(18.f * U32, sqrt_up(__fmul_rn(rb, ee)), 1e-30f));
     }
     V3 ne = rotB(S.B, T.n);
     out.set(12, ne.x);
     out.set(13, ne.y);
     out.set(14, ne.z);
     out.set(15, det);
-    out.set(16, det != 0.f ? err_det_abs * rcp_up(fabsf(det)) : 1.f);
+    out.set(16, det != 0.f ? __fmul_rn(err_det_abs, rcp_up(fabsf(det))) : 1.f);
     out.set(17, __uint_as_float(unc ? 1u : 0u));
-    float q0 = 3.f * (fabsf(T.n.x) + T.N.x), q1 = 3.f * (fabsf(T.n.y) + T.N.y), q2 = 3.f * (fabsf(T.n.z) + T.N.z);
-    out.set(18, U32 * (fabsf(S.B[0]) * q0 + fabsf(S.B[1]) * q1 + fabsf(S.B[2]) * q2 + 6.f * fabsf(ne.x)));
-    out.set(19, U32 * (fabsf(S.B[3]) * q0 + fabsf(S.B[4]) * q1 + fabsf(S.B[5]) * q2 + 6.f * fabsf(ne.y)));
-    out.set(20, U32 * (fabsf(S.B[6]) * q0 + fabsf(S.B[7]) * q1 + fabsf(S.B[8]) * q2 + 6.f * fabsf(ne.z)));
+    const V3 q = {__fmul_rn(3.f, __fadd_rn(fabsf(T.n.x), T.N.x)), __fmul_rn(3.f, __fadd_rn(fabsf(T.n.y), T.N.y)),
+                  __fmul_rn(3.f, __fadd_rn(fabsf(T.n.z), T.N.z))};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const V3 br = {fabsf(S.B[3 * r]), fabsf(S.B[3 * r + 1]), fabsf(S.B[3 * r + 2])};
+        const float ner = r == 0 ? ne.x : (r == 1 ? ne.y : ne.z);
+        out.set(18 + r, __fmul_rn(U32, __fmaf_rn(6.f, fabsf(ner), vdot(br, q))));
+    }
 }
 
 // FP32 error bound of det = w0.n used by the back-face cull (n = (v1-v0)x(v2-v0),
 // N the sums of |products| of its cross-product terms)
 __device__ __forceinline__ float backface_err(const V3& w0, const V3& n, const V3& N) {
-    return U32 * (fabsf(w0.x) * (3.f * N.x + 4.f * fabsf(n.x)) + fabsf(w0.y) * (3.f * N.y + 4.f * fabsf(n.y)) +
-                  fabsf(w0.z) * (3.f * N.z + 4.f * fabsf(n.z)));
+    const V3 aw = {fabsf(w0.x), fabsf(w0.y), fabsf(w0.z)};
+    const V3 c = {__fmaf_rn(3.f, N.x, __fmul_rn(4.f, fabsf(n.x))), __fmaf_rn(3.f, N.y, __fmul_rn(4.f, fabsf(n.y))),
+                  __fmaf_rn(3.f, N.z, __fmul_rn(4.f, fabsf(n.z)))};
+    return __fmul_rn(U32, vdot(aw, c));
 }
 
 __device__ __forceinline__ float det_error(const V3& w0, const TriW& T) {
-    return U32 * (fabsf(w0.x) * (3.f * T.N.x + 4.f * fabsf(T.n.x)) + fabsf(w0.y) * (3.f * T.N.y + 4.f * fabsf(T.n.y)) +
-                  fabsf(w0.z) * (3.f * T.N.z + 4.f * fabsf(T.n.z))) + 1e-35f;
+    return __fadd_rn(backface_err(w0, T.n, T.N), 1e-35f);
 }
 
 // ---------------------------------------------------------------------------
@@ -265,13 +273,15 @@ __device__ __forceinline__ int test_fp32(const SV& st, const SensorDev& S, V3 d,
         return T_MISS;
     }
     bool inside = E0 > tau0 && E1 > tau1 && E2 > tau2;
-    t_err = st.f(16) + (fabsf(d.x) * st.f(18) + fabsf(d.y) * st.f(19) + fabsf(d.z) * st.f(20)) * fabsf(rdn) + 2.4e-7f;
+    t_err = __fadd_rn(__fmaf_rn(vdot({fabsf(d.x), fabsf(d.y), fabsf(d.z)}, {st.f(18), st.f(19), st.f(20)}), fabsf(rdn),
+                                st.f(16)),
+                      2.4e-7f);
     if (!(t > 0.f) || !(t_err < 0.25f)) {
         t_err = 1.f;
         return (inside && !unc_pair && !(t > 0.f)) ? T_MISS : T_UNCERTAIN;
     }
     if (S.has_range) {
-        float lo = t * (1.f - t_err), hi = t * (1.f + t_err);
+        const float lo = __fmul_rn(t, __fsub_rn(1.f, t_err)), hi = __fmul_rn(t, __fadd_rn(1.f, t_err));
         if (hi < S.d_min || lo > S.d_max) return T_MISS;
         if (lo < S.d_min || hi > S.d_max) return T_UNCERTAIN;
     }
@@ -327,9 +337,10 @@ __device__ __forceinline__ int commit_pre(const CastArgs& a, uint32_t g, uint32_
     float tcur = __uint_as_float((uint32_t)(cur >> 32));
     if (res == T_UNCERTAIN) {
         // a re-test can only change the result if it may beat the current best
-        bool t_ok = t_err < 0.25f && t > 0.f;
-        if (t_ok && t * (1.f - t_err) > tcur * (1.f + BETA)) return 0;
-        push_recheck(a, g, tri, t_ok ? t * (1.f - t_err) : 0.f);
+        const bool t_ok = t_err < 0.25f && t > 0.f;
+        const float t_lo = __fmul_rn(t, __fsub_rn(1.f, t_err));
+        if (t_ok && t_lo > __fmul_rn(tcur, 1.f + BETA)) return 0;
+        push_recheck(a, g, tri, t_ok ? t_lo : 0.f);
         n_unc++;
         return 0;
     }
@@ -338,14 +349,14 @@ __device__ __forceinline__ int commit_pre(const CastArgs& a, uint32_t g, uint32_
         if (key < cur) atomicMin(kp, key);
         return 1;
     }
-    if (t > tcur * (1.f + BETA)) return 1;
+    if (t > __fmul_rn(tcur, 1.f + BETA)) return 1;
     unsigned long long old = atomicMin(kp, key);
     uint32_t oid = (uint32_t)old;
     if (oid != NO_HIT && oid != tri) {
         float told = __uint_as_float((uint32_t)(old >> 32));
-        if (fabsf(t - told) <= BETA * fmaxf(t, told)) {
-            push_recheck(a, g, tri, t * (1.f - TAU_T));
-            push_recheck(a, g, oid, told * (1.f - TAU_T));
+        if (fabsf(__fsub_rn(t, told)) <= __fmul_rn(BETA, fmaxf(t, told))) {
+            push_recheck(a, g, tri, __fmul_rn(t, 1.f - TAU_T));
+            push_recheck(a, g, oid, __fmul_rn(told, 1.f - TAU_T));
             n_ties++;
         }
     }
@@ -1313,9 +1324,12 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
     if (lane < 8) W.cnt[lane] = 0;
     uint32_t c_unc = 0, c_ties = 0, c_hits = 0;
     const uint32_t n = min(*(volatile uint32_t*)&a.qcount[Q_SURV], a.surv_cap);
+    // part 1 records how far it goes; part 2 starts there (a.surv_part)
+    const uint32_t s0 = a.surv_part == 2 ? min(*(volatile uint32_t*)&a.qcount[Q_SURV_SPLIT], n) : 0u;
+    if (a.surv_part == 1 && blockIdx.x == 0 && threadIdx.x == 0) a.qcount[Q_SURV_SPLIT] = n;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t gwarp = ((blockIdx.x * blockDim.x) >> 5) + wib;
-    for (uint32_t b0 = gwarp * 32; b0 < n; b0 += n_warps * 32) {
+    for (uint32_t b0 = s0 + gwarp * 32; b0 < n; b0 += n_warps * 32) {
         const uint32_t q = b0 + lane;
         uint32_t ncand = 0;
         uint32_t l_live = 0, l_cand = 0, l_big = 0, hit0 = 0, tested0 = 0;
@@ -1803,7 +1817,7 @@ __global__ void k_recheck_filter(CastArgs a) {
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
         uint4 e = a.recheck[q];
         float tbest = __uint_as_float((uint32_t)(a.keys[e.x] >> 32));
-        if (__uint_as_float(e.z) <= tbest * (1.f + BETA)) {
+        if (__uint_as_float(e.z) <= __fmul_rn(tbest, 1.f + BETA)) {
             flag_ray(a, e.x);
         } else {
             a.recheck[q].y = NO_HIT;
@@ -1886,27 +1900,34 @@ __global__ void k_decode(CastArgs a, int recheck) {
 
 // ---------------------------------------------------------------------------
 // k_bvh: the static side of the hybrid static/dynamic pipeline (Sec. 7).
-// One thread per ray walks the static hierarchy front to back (both child
-// boxes per node, the nearer child first, the farther one on a per-thread
-// stack).  Each leaf triangle takes the same pair setup, FP32 test and
-// closest-hit commit as the culled path, into the same u64 keys, so the
-// static and dynamic results merge on the GPU by the key minimum.  Subtrees
-// that start beyond the ray's best certain hit (dynamic or static, plus the
-// tie band) are skipped.
+// A warp takes 32 consecutive rays (32 adjacent azimuths of one channel, a
+// thin fan) and walks the static hierarchy once for all of them: every lane
+// tests its own ray against both child boxes, and the warp enters a child
+// if any lane's ray does (the nearer one first, by majority), keeping the
+// other on a per-warp stack in shared memory.  At a leaf every lane tests
+// its ray against the leaf's triangles: a cheap world-frame pre-test, then,
+// for the few that pass, the culled path's own pair setup, FP32 test and
+// closest-hit commit, into the same u64 keys, so static and dynamic results
+// merge on the GPU by the key minimum.  Each lane skips subtrees that start
+// beyond its best certain hit (dynamic or static, plus the tie band).
 // ---------------------------------------------------------------------------
+constexpr int BVH_BLOCK = 128;
 template <bool RECHECK>
-__global__ void __launch_bounds__(128, 4) k_bvh(CastArgs a) {
+__global__ void __launch_bounds__(BVH_BLOCK, 4) k_bvh(CastArgs a) {
+    __shared__ int32_t stk[BVH_BLOCK / 32][BVH_STACK];
+    const uint32_t lane = threadIdx.x & 31u;
+    int32_t* stack = stk[threadIdx.x >> 5];
     const bool cull_back = a.flags & 2u;
     uint32_t n_vis = 0, n_tst = 0, c_unc = 0, c_ties = 0;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    int32_t stack[BVH_STACK];
-    constexpr int32_t DONE = 0x7FFFFFFF;  // no inner node has this index (nodes < 2^27)
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_rays_total; g += stride) {
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t g0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; g0 < a.n_rays_total; g0 += n_warps * 32u) {
+        const uint32_t g = g0 + lane;
+        const bool valid = g < a.n_rays_total;
         uint32_t sn = 0;
         for (uint32_t k = 1; k < a.n_sensors; ++k)
             if (a.sensors[k].ray_off <= g) sn = k;
         const SensorDev& S = a.sensors[sn];
-        const uint32_t q = g - S.ray_off;
+        const uint32_t q = valid ? g - S.ray_off : 0u;
         const uint32_t j = q / S.n_rays, i = q - j * S.n_rays;
         const V3 d = ray_dir(__ldg(&a.ch_sc[S.ch_off + j]), __ldg(&a.az_sc[S.az_off + i]));
         // world direction B^T d for the box tests and the leaf pre-test (the exact test uses d)
@@ -1917,14 +1938,16 @@ __global__ void __launch_bounds__(128, 4) k_bvh(CastArgs a) {
         const V3 o = {S.o_hi[0], S.o_hi[1], S.o_hi[2]};
         // pre-test margin term of the origin's low part (|o_lo| <= u |o|)
         const float o_term = 2.f * U32 * (fabsf(o.x) + fabsf(o.y) + fabsf(o.z));
-        unsigned long long cur = __ldcg(&a.keys[g]);
+        unsigned long long cur = valid ? __ldcg(&a.keys[g]) : 0ull;
         const float tmin = fmaxf(S.d_min * (1.f - 2e-5f) - 2e-6f, 0.f);
-        float tmax = fminf(S.d_max * (1.f + 2e-5f) + 2e-6f, __uint_as_float((uint32_t)(cur >> 32)) * (1.f + 4.f * BETA));
-        int sp = 0;
-        int32_t node = 0;
-        while (node != DONE) {
-            // inner nodes until a leaf is in hand (the warp then tests leaves together)
-            while (node >= 0 && node != DONE) {
+        // an idle lane gets an empty interval: it never votes for a box
+        float tmax = valid ? fminf(S.d_max * (1.f + 2e-5f) + 2e-6f,
+                                   __uint_as_float((uint32_t)(cur >> 32)) * (1.f + 4.f * BETA))
+                           : -1.f;
+        int sp = 0;          // warp-uniform
+        int32_t node = 0;    // warp-uniform
+        while (true) {
+            if (node >= 0) {
                 const float4* np = reinterpret_cast<const float4*>(a.bvh_nodes + node);
                 const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2);
                 const int4 n3 = __ldg(reinterpret_cast<const int4*>(np) + 3);
@@ -1941,22 +1964,30 @@ __global__ void __launch_bounds__(128, 4) k_bvh(CastArgs a) {
                 const float tn1 = fmaxf(fmaxf(fminf(ax1, bx1), fminf(ay1, by1)), fmaxf(fminf(az1, bz1), tmin));
                 const float tf1 = fminf(fminf(fmaxf(ax1, bx1), fmaxf(ay1, by1)), fminf(fmaxf(az1, bz1), tmax));
                 const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
-                if (h0 && h1) {
-                    const bool swap = tn1 < tn0;
-                    stack[sp++] = swap ? n3.x : n3.y;  // depth < BVH_STACK (checked at build)
+                const uint32_t b0 = __ballot_sync(0xffffffffu, h0), b1 = __ballot_sync(0xffffffffu, h1);
+                if (b0 && b1) {
+                    // child 1 first if most lanes that enter both find it nearer (or, when
+                    // no lane enters both, if more lanes enter it)
+                    const uint32_t both = b0 & b1, near1 = __ballot_sync(0xffffffffu, h0 && h1 && tn1 < tn0);
+                    const bool swap = both ? 2 * __popc(near1) > __popc(both) : __popc(b1) > __popc(b0);
+                    if (lane == 0) stack[sp] = swap ? n3.x : n3.y;  // depth < BVH_STACK (checked at build)
+                    __syncwarp();
+                    ++sp;
                     node = swap ? n3.y : n3.x;
-                } else if (h0 || h1) {
-                    node = h0 ? n3.x : n3.y;
+                } else if (b0 || b1) {
+                    node = b0 ? n3.x : n3.y;
                 } else {
-                    node = sp ? stack[--sp] : DONE;
+                    if (sp == 0) break;
+                    node = stack[--sp];
                 }
+                continue;
             }
-            if (node == DONE) break;
             const uint32_t lf = ((uint32_t)node >> 3) & 0x0FFFFFFFu, cnt = ((uint32_t)node & 7u) + 1u;
             for (uint32_t k = lf; k < lf + cnt; ++k) {
                 float t9[9];
 #pragma unroll
                 for (int m = 0; m < 9; ++m) t9[m] = __ldg(a.bvh_tris + 9ull * k + m);
+                if (!(tmax >= tmin)) continue;  // idle lane
                 n_tst++;
                 {
                     // world-frame pre-test: the edge functions F_k = dw.((v_k - o) x (v_k+1 - v_k))
@@ -2001,14 +2032,16 @@ __global__ void __launch_bounds__(128, 4) k_bvh(CastArgs a) {
                     tmax = fminf(tmax, t * (1.f + 4.f * BETA));
                 }
             }
-            node = sp ? stack[--sp] : DONE;
+            if (sp == 0) break;
+            node = stack[--sp];
         }
+        __syncwarp();
     }
-    n_vis = __reduce_add_sync(0xffffffffu, n_vis);
+    n_vis = __reduce_add_sync(0xffffffffu, lane == 0 ? n_vis : 0u);
     n_tst = __reduce_add_sync(0xffffffffu, n_tst);
     c_unc = __reduce_add_sync(0xffffffffu, c_unc);
     c_ties = __reduce_add_sync(0xffffffffu, c_ties);
-    if ((threadIdx.x & 31u) == 0) {
+    if (lane == 0) {
         if (n_vis) atomicAdd(&a.counters[C_BVH_VISITS], (unsigned long long)n_vis);
         if (n_tst) atomicAdd(&a.counters[C_BVH_TESTS], (unsigned long long)n_tst);
         if (c_unc) atomicAdd(&a.counters[C_UNCERTAIN], (unsigned long long)c_unc);
@@ -2092,16 +2125,17 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
         mark(K_INIT, 1);
         launches++;
     }
-    const bool do_b = split.part != 1;
+    CastArgs ab = a;
+    ab.surv_part = (uint32_t)split.part;
     if (recheck && brute)
-        launch_cull_split<true, true>(a, ac, true, do_b, cfg, n_sm, st, mark);
+        launch_cull_split<true, true>(ab, ac, true, true, cfg, n_sm, st, mark);
     else if (recheck)
-        launch_cull_split<true, false>(a, ac, true, do_b, cfg, n_sm, st, mark);
+        launch_cull_split<true, false>(ab, ac, true, true, cfg, n_sm, st, mark);
     else if (brute)
-        launch_cull_split<false, true>(a, ac, true, do_b, cfg, n_sm, st, mark);
+        launch_cull_split<false, true>(ab, ac, true, true, cfg, n_sm, st, mark);
     else
-        launch_cull_split<false, false>(a, ac, true, do_b, cfg, n_sm, st, mark);
-    launches += do_b ? 2 : 1;
+        launch_cull_split<false, false>(ab, ac, true, true, cfg, n_sm, st, mark);
+    launches += 2;
     if (split.part == 1) return launches;
     if (!brute) {
         mark(K_EXPAND, 0);
@@ -2118,12 +2152,12 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
     if (a.bvh_nodes) {
         // static side of a hybrid cast, after the dynamic triangles so that
         // their hits bound the traversal
-        const int blocks = (int)std::min<uint32_t>((a.n_rays_total + 127) / 128, (uint32_t)n_sm * 16);
+        const int blocks = (int)std::min<uint32_t>((a.n_rays_total + BVH_BLOCK - 1) / BVH_BLOCK, (uint32_t)n_sm * 16);
         mark(K_BVH, 0);
         if (recheck)
-            k_bvh<true><<<std::max(blocks, 1), 128, 0, st>>>(a);
+            k_bvh<true><<<std::max(blocks, 1), BVH_BLOCK, 0, st>>>(a);
         else
-            k_bvh<false><<<std::max(blocks, 1), 128, 0, st>>>(a);
+            k_bvh<false><<<std::max(blocks, 1), BVH_BLOCK, 0, st>>>(a);
         mark(K_BVH, 1);
         launches++;
     }

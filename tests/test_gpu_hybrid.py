@@ -3,8 +3,13 @@ triangles go through a bounding-volume hierarchy traced per ray, the dynamic
 ones through the culls, and both commit into the same closest-hit keys.
 
 The hierarchy is an acceleration, so the bar is the culled path's result:
-bit-identical outputs with GRCA_CAST_NO_STATIC_BVH (same FP32 test, same
-FP64 re-test), and zero errors against the FP64 oracle.
+the same triangle on every ray as with GRCA_CAST_NO_STATIC_BVH (same FP32
+test, same FP64 re-test), and zero errors against the FP64 oracle.  The
+distance may differ in the last bits on rays where one path sends an extra
+candidate to the FP64 re-test: the traversal skips subtrees beyond a ray's
+best certain hit, the culls test every candidate, and a re-tested ray
+reports the FP64 distance rounded to FP32 instead of the FP32 one (both
+within the FP32 bound 4e-6 of each other).
 """
 import numpy as np
 import pytest
@@ -32,6 +37,16 @@ def _both(c, ids, flags):
     return d, t, st, d0, t0, st0
 
 
+def _agree(d, t, d0, t0):
+    """Same triangle on every ray; distances equal up to the FP32 bound."""
+    assert np.array_equal(t, t0), np.count_nonzero(t != t0)
+    both = np.isfinite(d0)
+    assert np.array_equal(np.isfinite(d), both)
+    rel = np.abs(d[both].astype(np.float64) - d0[both]) / d0[both]
+    assert rel.max(initial=0.0) <= 5e-6, rel.max()
+    assert np.count_nonzero(rel) <= max(10, len(rel) // 1000)
+
+
 def _grade(sensors, tris, d, t, rays=None, cull=False):
     orc = oracle.Oracle(sensors)
     ref = oracle.cast(orc, tris, rays, cull_backface=cull, ties=True)
@@ -52,7 +67,7 @@ def test_hybrid_c1_all_static_all_rays(flags_name):
     d, t, st, d0, t0, st0 = _both(c, ids, fl)
     assert st["bvh_node_visits"] > 0 and st["pairs"] == 0
     assert st0["bvh_node_visits"] == 0
-    assert np.array_equal(t, t0) and np.array_equal(d, d0)
+    _agree(d, t, d0, t0)
     if fl & grca.CAST_FP64_RECHECK:
         g = _grade(sc.sensors, tris, d, t, cull=bool(fl & grca.CAST_CULL_BACKFACE))
         assert g["errors"] == 0, g
@@ -79,7 +94,7 @@ def test_hybrid_static_plus_dynamic_frames(cfg, d_max):
         d, t, st, d0, t0, st0 = _both(c, ids, fl)
         assert st["bvh_node_visits"] > 0
         assert st["pairs"] == (tris.shape[0] - ns) * len(ids)
-        assert np.array_equal(t, t0) and np.array_equal(d, d0), np.count_nonzero(t != t0)
+        _agree(d, t, d0, t0)
     g = _grade(sc.sensors, tris, d, t, rays=stratified_rays(sc.sensors, 300, seed=2))
     assert g["errors"] == 0, g
 
@@ -107,7 +122,7 @@ def test_hybrid_stale_after_static_update_and_rebuild():
     c.build_static(ns)
     d2, t2 = _cast(c, ids, fl)
     assert c.stats()["bvh_node_visits"] > 0
-    assert np.array_equal(t, t2) and np.array_equal(d, d2)
+    _agree(d2, t2, d, t)
     assert np.count_nonzero((t2 >= 100) & (t2 < 164)) > 0
     c.build_static(0)                                   # drop the hierarchy
     d3, t3 = _cast(c, ids, fl)
@@ -129,7 +144,7 @@ def test_hybrid_with_sensor_variants():
     c.set_range_noise(ids[2], 0.03, 5)
     d, t, st, d0, t0, st0 = _both(c, ids, grca.CAST_FP64_RECHECK)
     assert st["bvh_node_visits"] > 0
-    assert np.array_equal(t, t0) and np.array_equal(d, d0)
+    _agree(d, t, d0, t0)
 
 
 def test_build_static_rejects_bad_count():
