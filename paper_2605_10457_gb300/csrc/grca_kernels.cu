@@ -1914,9 +1914,10 @@ __global__ void k_decode(CastArgs a, int recheck) {
 constexpr int BVH_BLOCK = 128;
 template <bool RECHECK>
 __global__ void __launch_bounds__(BVH_BLOCK, 4) k_bvh(CastArgs a) {
-    __shared__ int32_t stk[BVH_BLOCK / 32][BVH_STACK];
+    // per-warp stack of (deferred child, lanes whose rays enter its box)
+    __shared__ int2 stk[BVH_BLOCK / 32][BVH_STACK];
     const uint32_t lane = threadIdx.x & 31u;
-    int32_t* stack = stk[threadIdx.x >> 5];
+    int2* stack = stk[threadIdx.x >> 5];
     const bool cull_back = a.flags & 2u;
     uint32_t n_vis = 0, n_tst = 0, c_unc = 0, c_ties = 0;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
@@ -1946,7 +1947,11 @@ __global__ void __launch_bounds__(BVH_BLOCK, 4) k_bvh(CastArgs a) {
                            : -1.f;
         int sp = 0;          // warp-uniform
         int32_t node = 0;    // warp-uniform
-        while (true) {
+        // lanes whose rays enter the current node's box (a lane outside it
+        // cannot enter any box below it: the boxes are nested)
+        uint32_t act = __ballot_sync(0xffffffffu, tmax >= tmin);
+        while (act) {
+            const bool mine = (act >> lane) & 1u;
             if (node >= 0) {
                 const float4* np = reinterpret_cast<const float4*>(a.bvh_nodes + node);
                 const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2);
@@ -1963,22 +1968,26 @@ __global__ void __launch_bounds__(BVH_BLOCK, 4) k_bvh(CastArgs a) {
                 const float tf0 = fminf(fminf(fmaxf(ax0, bx0), fmaxf(ay0, by0)), fminf(fmaxf(az0, bz0), tmax));
                 const float tn1 = fmaxf(fmaxf(fminf(ax1, bx1), fminf(ay1, by1)), fmaxf(fminf(az1, bz1), tmin));
                 const float tf1 = fminf(fminf(fmaxf(ax1, bx1), fmaxf(ay1, by1)), fminf(fmaxf(az1, bz1), tmax));
-                const bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
+                const bool h0 = mine && tn0 <= tf0, h1 = mine && tn1 <= tf1;
                 const uint32_t b0 = __ballot_sync(0xffffffffu, h0), b1 = __ballot_sync(0xffffffffu, h1);
                 if (b0 && b1) {
                     // child 1 first if most lanes that enter both find it nearer (or, when
                     // no lane enters both, if more lanes enter it)
                     const uint32_t both = b0 & b1, near1 = __ballot_sync(0xffffffffu, h0 && h1 && tn1 < tn0);
                     const bool swap = both ? 2 * __popc(near1) > __popc(both) : __popc(b1) > __popc(b0);
-                    if (lane == 0) stack[sp] = swap ? n3.x : n3.y;  // depth < BVH_STACK (checked at build)
+                    if (lane == 0) stack[sp] = swap ? make_int2(n3.x, (int)b0) : make_int2(n3.y, (int)b1);  // depth < BVH_STACK
                     __syncwarp();
                     ++sp;
                     node = swap ? n3.y : n3.x;
+                    act = swap ? b1 : b0;
                 } else if (b0 || b1) {
                     node = b0 ? n3.x : n3.y;
+                    act = b0 ? b0 : b1;
                 } else {
                     if (sp == 0) break;
-                    node = stack[--sp];
+                    const int2 e = stack[--sp];
+                    node = e.x;
+                    act = (uint32_t)e.y;
                 }
                 continue;
             }
@@ -1987,7 +1996,7 @@ __global__ void __launch_bounds__(BVH_BLOCK, 4) k_bvh(CastArgs a) {
                 float t9[9];
 #pragma unroll
                 for (int m = 0; m < 9; ++m) t9[m] = __ldg(a.bvh_tris + 9ull * k + m);
-                if (!(tmax >= tmin)) continue;  // idle lane
+                if (!mine || !(tmax >= tmin)) continue;  // this lane's ray misses the leaf's box
                 n_tst++;
                 {
                     // world-frame pre-test: the edge functions F_k = dw.((v_k - o) x (v_k+1 - v_k))
@@ -2033,7 +2042,9 @@ __global__ void __launch_bounds__(BVH_BLOCK, 4) k_bvh(CastArgs a) {
                 }
             }
             if (sp == 0) break;
-            node = stack[--sp];
+            const int2 e = stack[--sp];
+            node = e.x;
+            act = (uint32_t)e.y;
         }
         __syncwarp();
     }
