@@ -805,6 +805,9 @@ static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, f
         }
         const double t_far = std::min(std::sqrt(far2), d.d_max);
         if (!(BVH_RAY_ETA * t_far <= ctx->bvh_delta)) hybrid = false;
+        // the origin's own coordinates enter the slab rounding as well
+        const double omax = std::max(std::fabs(d.origin[0]), std::max(std::fabs(d.origin[1]), std::fabs(d.origin[2])));
+        if (!(omax * 0x1p-21 <= 0.5 * ctx->bvh_delta)) hybrid = false;
     }
     if (hybrid) {
         a.tri_first = ctx->n_static;

@@ -249,7 +249,13 @@ bool build_bvh(const float* tris, uint32_t n, BvhHost& out) {
         out.scene_lo[k] = scene.lo[k];
         out.scene_hi[k] = scene.hi[k];
     }
-    out.delta = BVH_ETA * (std::sqrt(diag2) + 1.0);
+    // plus 2^-21 of the largest coordinate: the FP32 slab distances are formed
+    // as x / d - o / d, whose rounding is a few ulps of the coordinates
+    double cmax = 0.0;
+    for (int k = 0; k < 3; ++k)
+        if (std::isfinite(scene.lo[k]))
+            cmax = std::max(cmax, std::max(std::fabs((double)scene.lo[k]), std::fabs((double)scene.hi[k])));
+    out.delta = BVH_ETA * (std::sqrt(diag2) + 1.0) + cmax * 0x1p-21;
     const double d = out.delta;
     for (BvhNode& nd : out.nodes) {
         float* f = reinterpret_cast<float*>(&nd);

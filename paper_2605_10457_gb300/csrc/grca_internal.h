@@ -210,7 +210,9 @@ struct BvhNode {
 static_assert(sizeof(BvhNode) == 64, "one node = four 16-byte loads");
 constexpr uint32_t BVH_LEAF_MAX = 8;
 constexpr int BVH_STACK = 64;
-// Boxes are inflated outward by delta = BVH_ETA * (scene diagonal + 1).  A
+// Boxes are inflated outward by delta = BVH_ETA * (scene diagonal + 1) +
+// 2^-21 * (largest scene coordinate), the last term for the rounding of the
+// slab distances.  A
 // candidate that the FP32 test can report as a hit or send to the FP64
 // re-test lies within ~2e-6 t of the FP32 ray at distance t (table and
 // rotation rounding of the direction, the test's error bounds), so the

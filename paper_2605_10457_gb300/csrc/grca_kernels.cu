@@ -1937,6 +1937,7 @@ __global__ void __launch_bounds__(BVH_BLOCK, 4) k_bvh(CastArgs a) {
         const V3 inv = {1.f / (dw.x != 0.f ? dw.x : 1e-30f), 1.f / (dw.y != 0.f ? dw.y : 1e-30f),
                         1.f / (dw.z != 0.f ? dw.z : 1e-30f)};
         const V3 o = {S.o_hi[0], S.o_hi[1], S.o_hi[2]};
+        const V3 oi = {o.x * inv.x, o.y * inv.y, o.z * inv.z};
         // pre-test margin term of the origin's low part (|o_lo| <= u |o|)
         const float o_term = 2.f * U32 * (fabsf(o.x) + fabsf(o.y) + fabsf(o.z));
         unsigned long long cur = valid ? __ldcg(&a.keys[g]) : 0ull;
@@ -1957,13 +1958,14 @@ __global__ void __launch_bounds__(BVH_BLOCK, 4) k_bvh(CastArgs a) {
                 const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2);
                 const int4 n3 = __ldg(reinterpret_cast<const int4*>(np) + 3);
                 n_vis++;
-                // slab distances (x - o) / dw; the boxes are inflated to absorb the rounding
-                const float ax0 = (n0.x - o.x) * inv.x, bx0 = (n0.w - o.x) * inv.x;
-                const float ay0 = (n0.y - o.y) * inv.y, by0 = (n1.x - o.y) * inv.y;
-                const float az0 = (n0.z - o.z) * inv.z, bz0 = (n1.y - o.z) * inv.z;
-                const float ax1 = (n1.z - o.x) * inv.x, bx1 = (n2.y - o.x) * inv.x;
-                const float ay1 = (n1.w - o.y) * inv.y, by1 = (n2.z - o.y) * inv.y;
-                const float az1 = (n2.x - o.z) * inv.z, bz1 = (n2.w - o.z) * inv.z;
+                // slab distances x / dw - o / dw (one FMA each); their rounding, relative to
+                // |o| + |x - o| along the ray, is far below the boxes' inflation
+                const float ax0 = fmaf(n0.x, inv.x, -oi.x), bx0 = fmaf(n0.w, inv.x, -oi.x);
+                const float ay0 = fmaf(n0.y, inv.y, -oi.y), by0 = fmaf(n1.x, inv.y, -oi.y);
+                const float az0 = fmaf(n0.z, inv.z, -oi.z), bz0 = fmaf(n1.y, inv.z, -oi.z);
+                const float ax1 = fmaf(n1.z, inv.x, -oi.x), bx1 = fmaf(n2.y, inv.x, -oi.x);
+                const float ay1 = fmaf(n1.w, inv.y, -oi.y), by1 = fmaf(n2.z, inv.y, -oi.y);
+                const float az1 = fmaf(n2.x, inv.z, -oi.z), bz1 = fmaf(n2.w, inv.z, -oi.z);
                 const float tn0 = fmaxf(fmaxf(fminf(ax0, bx0), fminf(ay0, by0)), fmaxf(fminf(az0, bz0), tmin));
                 const float tf0 = fminf(fminf(fmaxf(ax0, bx0), fmaxf(ay0, by0)), fminf(fmaxf(az0, bz0), tmax));
                 const float tn1 = fmaxf(fmaxf(fminf(ax1, bx1), fminf(ay1, by1)), fmaxf(fminf(az1, bz1), tmin));
