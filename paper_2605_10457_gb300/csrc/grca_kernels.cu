@@ -676,6 +676,12 @@ __device__ __forceinline__ bool elev_range_w(const SensorDev& S, const V3 w[3], 
         if (fmaxf(z[0], fmaxf(z[1], z[2])) > 0.f) smax = 1.f;
         if (fminf(z[0], fminf(z[1], z[2])) < 0.f) smin = -1.f;
     }
+    if (!(r2max < 3e38f)) {
+        // a vertex so far away that |w|^2 overflows: every channel, full circle
+        smin = -1.f;
+        smax = 1.f;
+        pierced = true;
+    }
     return pierced;
 }
 
@@ -1116,6 +1122,9 @@ __device__ __forceinline__ void flush_survivors(const CastArgs& a, CullAWarpSmem
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool group_may_hit(const SensorDev& S, const float* sins, const uint16_t* lut,
                                               const float4& lo, const float4& hi) {
+    // a box with an infinite side (a member with an infinite vertex) bounds
+    // nothing useful: keep the group
+    if (!isfinite(lo.x + lo.y + lo.z + hi.x + hi.y + hi.z)) return true;
     // rounding of w = (v - o_hi) - o_lo is monotone in v, so every member
     // vertex, transformed like the triangles, lies inside [wl, wh]
     const V3 wl = rel_origin(S, V3{lo.x, lo.y, lo.z}), wh = rel_origin(S, V3{hi.x, hi.y, hi.z});
@@ -1134,7 +1143,7 @@ __device__ __forceinline__ bool group_may_hit(const SensorDev& S, const float* s
     const float R = sqrtf(vdot(h, h)) * (1.f + 1e-6f) + 2e-7f * (fabsf(c.x) + fabsf(c.y) + fabsf(c.z));
     const float D2 = vdot(c, c);
     // near or large spheres (half-angle above ~82 deg): keep, the bound is loose there
-    if (!(D2 > 0.f) || R * R > 0.98f * D2) return true;
+    if (!(D2 > 0.f) || !(D2 < 3e38f) || R * R > 0.98f * D2) return true;
     const float invD = rsqrtf(D2);
     // centre elevation from the sensor frame (no cancellation near the poles)
     const float cx = S.B[0] * c.x + S.B[1] * c.y + S.B[2] * c.z, cy = S.B[3] * c.x + S.B[4] * c.y + S.B[5] * c.z,

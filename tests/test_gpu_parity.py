@@ -305,6 +305,34 @@ def test_sixty_four_sensors_in_one_cast():
         c.cast(ids + [ids[0]], CAST_FP64_RECHECK)        # 65 sensors: rejected
 
 
+def test_non_finite_vertices_never_hit():
+    """Triangles with NaN or infinite vertices never hit (the oracle's plane and
+    edge tests fail on them) and do not disturb the culls, the spans, the
+    group boxes or the hierarchy: every other ray matches the oracle."""
+    from paper_2605_10457_gb300.grca import CAST_FP64_RECHECK
+    sc = scene_c1()
+    tris = sc.tris(0).copy()
+    rng = np.random.default_rng(9)
+    bad = rng.choice(tris.shape[0], 300, replace=False)
+    vals = np.array([np.nan, np.inf, -np.inf], np.float32)
+    for k, b in enumerate(bad):
+        tris[b, k % 3, (k // 3) % 3] = vals[k % 3]
+
+    for d_max, hybrid in ((np.inf, False), (12.0, False), (np.inf, True)):
+        sens = [make_sensor((0.0, 0.0, 1.8), channels="uniform16", n_rays=512, d_min=0.0, d_max=d_max)]
+        c = _caster()
+        ids = [c.add_sensor(s) for s in sens]
+        c.upload(tris)
+        if hybrid:
+            c.build_static(tris.shape[0])
+        d, t = _cast(c, ids, CAST_FP64_RECHECK)
+        assert c.stats()["device_error"] == 0
+        assert not np.isin(t, bad).any()
+        S = type("S", (), {"sensors": sens})
+        g = _check(S, tris, d, t)
+        assert g["errors"] == 0, (d_max, hybrid, g)
+
+
 def test_capacity_overflow_is_reported():
     from paper_2605_10457_gb300.grca import CAST_FP64_RECHECK
     sc = scene_c1()
