@@ -286,6 +286,7 @@ def main():
     tune_ms = None
     if not args.no_autotune:
         tune_ms = c.autotune(ids, FL, out)
+    launch_cfg = c.launch_config(ids, FL)
 
     def step_batched(k):
         f = frame_of(rank, ws, k, args.frames)
@@ -336,7 +337,7 @@ def main():
     if args.lean:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": whole_job_rate(ws, n_rays, args.steps, ms_b / 1e3),
-                              "unit": "Mrays/s", "ms_per_step": ms_b / args.steps, "lean": True,
+                              "unit": "Mrays/s", "ms_per_step": ms_b / args.steps, "lean": True, "launch_config": launch_cfg,
                               "stats": st, "clocks": clocks}), flush=True)
         c.close()
         return 0
@@ -383,13 +384,16 @@ def main():
         t_b = time.time()
         c.build_static(ns)
         hb_s = time.time() - t_b
+        if not args.no_autotune:
+            c.autotune(ids, FL, out)
         ms_h = timed(step_batched, args.steps, args.warmup)
         st_h = c.stats(check=False)
         hybrid = {"value": whole_job_rate(ws, n_rays, args.steps, ms_h / 1e3), "unit": "Mrays/s",
                   "ms_per_step": ms_h / args.steps, "static_build_s": hb_s,
                   "path": f"{ns} static triangles through a hierarchy built once (warp-packet traversal), "
                           f"{nd} dynamic through the culls, FP32 + FP64 recheck, one key minimum",
-                  "bvh_node_visits": st_h.get("bvh_node_visits"), "bvh_tests": st_h.get("bvh_tests")}
+                  "bvh_node_visits": st_h.get("bvh_node_visits"), "bvh_tests": st_h.get("bvh_tests"),
+                  "launch_config": c.launch_config(ids, FL)}
         c.build_static(0)
 
     # --- roofline of the dominant kernel ---------------------------------------
@@ -465,6 +469,7 @@ def main():
                                           "chunks", "tests", "hits", "uncertain", "ties", "flagged_rays",
                                           "recheck_pairs")},
         "autotune_ms": tune_ms,
+        "launch_config": launch_cfg,
         "static_build_s": build_s,
         "device_error": st_prof["device_error"],
     }

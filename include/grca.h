@@ -209,6 +209,14 @@ grca_status grca_cast_host(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_
 grca_status grca_autotune(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_sensors, float* out_dist,
                           uint32_t* out_tri, uint32_t flags, void* stream, float* out_ms);
 
+/* The launch configuration a cast of these sensors with these flags would
+ * use now (tuned by grca_autotune for this cast shape, else the context's
+ * default): out[0] inline candidate limit, out[1] chunk size in rays,
+ * out[2] culling block size, out[3] culling blocks per SM.  Returns
+ * GRCA_ERR_INVALID_ARG for bad ids, counts or flags. */
+grca_status grca_get_launch_config(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_sensors, uint32_t flags,
+                                  int32_t out[4]);
+
 /* Hybrid static/dynamic pipeline (Sec. 7): build a bounding-volume hierarchy
  * over triangles [0, n_static) of the uploaded set (binned SAH on the host,
  * once; blocks until done).  Casts then trace those triangles through the

@@ -818,9 +818,14 @@ static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, f
     return GRCA_OK;
 }
 
+// launch configurations are tuned per cast shape: sensors, rays, triangles
+// through the culls, and the flags that change the work (not GRAPH or DUMP)
+static std::tuple<uint32_t, uint32_t, uint32_t, uint32_t> tune_key(const CastArgs& a) {
+    return std::make_tuple(a.n_sensors, a.n_rays_total, a.n_tris - a.tri_first, a.flags & 0xE7u);
+}
+
 static LaunchCfg cfg_for(grca_ctx* ctx, const CastArgs& a) {
-    auto key = std::make_tuple(a.n_sensors, a.n_rays_total, a.n_tris - a.tri_first, a.flags & 0xE7u);
-    auto it = ctx->tuned.find(key);
+    auto it = ctx->tuned.find(tune_key(a));
     return it == ctx->tuned.end() ? ctx->cfg : it->second;
 }
 
@@ -1046,6 +1051,32 @@ grca_status grca_profile_read(grca_ctx* ctx, uint32_t max, const char** names, u
     return GRCA_OK;
 }
 
+grca_status grca_get_launch_config(grca_ctx* ctx, const int32_t* ids, uint32_t n, uint32_t flags,
+                                  int32_t out[4]) {
+    if (!ctx || !out) return GRCA_ERR_INVALID_ARG;
+    if (!ids || n < 1 || n > (uint32_t)MAX_SENSORS || (flags & ~0xFFu)) return GRCA_ERR_INVALID_ARG;
+    uint32_t rays = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        if (ids[k] < 0 || ids[k] >= (int32_t)ctx->sensors.size()) return GRCA_ERR_INVALID_ARG;
+        rays += ctx->sensors[ids[k]].d.n_channels * ctx->sensors[ids[k]].d.n_rays;
+    }
+    CastArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n_sensors = n;
+    a.n_rays_total = rays;
+    a.n_tris = ctx->n_tris;
+    a.flags = flags & ~(uint32_t)(GRCA_CAST_GRAPH | GRCA_CAST_DUMP_CANDIDATES);
+    const bool hybrid = ctx->d_bvh_nodes && !ctx->bvh_stale && ctx->n_static &&
+                        !(flags & (GRCA_CAST_BRUTE | GRCA_CAST_LOSSY_AREA | GRCA_CAST_DUMP_CANDIDATES | GRCA_CAST_NO_STATIC_BVH));
+    a.tri_first = hybrid ? ctx->n_static : 0;
+    const LaunchCfg c = cfg_for(ctx, a);
+    out[0] = c.inline_max;
+    out[1] = c.chunk_rays;
+    out[2] = c.cull_block;
+    out[3] = c.cull_blocks_per_sm;
+    return GRCA_OK;
+}
+
 grca_status grca_autotune(grca_ctx* ctx, const int32_t* ids, uint32_t n, float* out_dist, uint32_t* out_tri,
                           uint32_t flags, void* stream, float* out_ms) {
     if (!ctx) return GRCA_ERR_INVALID_ARG;
@@ -1113,7 +1144,7 @@ grca_status grca_autotune(grca_ctx* ctx, const int32_t* ids, uint32_t n, float* 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rs != GRCA_OK) return rs;
-    ctx->tuned[std::make_tuple(a.n_sensors, a.n_rays_total, a.n_tris, fl & 0x27u)] = best;
+    ctx->tuned[tune_key(a)] = best;
     if (out_ms) *out_ms = best_ms;
     // leave the outputs holding a valid frame from the chosen configuration
     CastArgs b = a;

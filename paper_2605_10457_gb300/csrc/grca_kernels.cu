@@ -4,19 +4,27 @@
 // count from device memory, so the sequence is capturable as a CUDA graph):
 //   k_init     key init (+inf, no id), clear the per-ray flag bits and queue
 //              counters (Sec. A.5.1 ray-setup pass).
-//   k_cull     persistent over triangles x sensors: emitter transform,
-//              back-face / range culls (App. A.4.1 Step 1), channel span from
-//              the exact elevation extent (replaces the binary search of
-//              Sec. 3.6), azimuth span from the vertex projections
-//              (Sec. 3.7), then either inline tests (small spans) or a
-//              warp-aggregated append to the deferred queue (App. A.6, BAT
+//   k_cull_a   every (triangle, sensor) pair: group-level cull of 32-triangle
+//              tiles (GACP-T_g, Sec. 10.1.1) when a range is set, emitter
+//              transform, back-face / range culls (App. A.4.1 Step 1) and the
+//              channel span from the exact elevation extent (replaces the
+//              binary search of Sec. 3.6); survivors go to a queue, sorted by
+//              sensor per warp flush.
+//   k_cull_b   every survivor, warp-cooperative: azimuth span from the vertex
+//              projections (Sec. 3.7), then the pair setup and inline tests of
+//              small spans, or an append to the deferred queue (App. A.6, BAT
 //              list with ballot/popc allocation).
 //   k_expand   deferred pairs: per-channel cone/plane crossings give exact
 //              per-channel azimuth spans (Sec. 3.5, App. A.4.2 Step 1);
 //              rows are cut into fixed-size chunks of a device work queue.
 //   k_test     one warp per chunk: watertight FP32 test + closest-hit key.
+//   k_bvh      hybrid casts only (Sec. 7): warp-packet traversal of the static
+//              hierarchy, committing into the same keys.
 //   k_recheck_*  FP64 re-test of every ray the FP32 pass flagged.
-//   k_decode   key -> (distance, triangle id) (Sec. A.5.1 output pass).
+//   k_decode   key -> (distance, triangle id) (Sec. A.5.1 output pass), ray
+//              masks and range noise (App. A.3, App. A.1).
+// k_cull (fused phase A + B) and k_noalloc_prepare serve the allocation-free
+// entry point; k_group_bounds runs before a cast that culls by group.
 //
 // Ray-triangle test.  The paper uses Moller-Trumbore (App. A.4.1 Step 5).
 // Here the test is watertight: edge functions E_k = d . (a_k x b_k) of the

@@ -66,7 +66,8 @@ EXPORTS = ["grca_create", "grca_destroy", "grca_create_sensor", "grca_set_sensor
            "grca_update_vertices", "grca_cast", "grca_cast_host", "grca_autotune", "grca_set_debug_dump",
            "grca_get_stats", "grca_last_launch_count", "grca_profile_enable", "grca_profile_read",
            "grca_status_string", "grca_last_cuda_error", "grca_cast_noalloc",
-           "grca_set_ray_mask", "grca_set_sensor_azimuths", "grca_set_range_noise", "grca_build_static"]
+           "grca_set_ray_mask", "grca_set_sensor_azimuths", "grca_set_range_noise", "grca_build_static",
+           "grca_get_launch_config"]
 
 
 def library_path() -> str:
@@ -113,6 +114,8 @@ def _lib_handle(build_if_missing: bool = True):
     lib.grca_profile_read.argtypes = [P, u32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_uint64),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32)]
     lib.grca_profile_read.restype = i32
+    lib.grca_get_launch_config.argtypes = [P, P, u32, u32, P]
+    lib.grca_get_launch_config.restype = i32
     lib.grca_build_static.argtypes = [P, u32, P]
     lib.grca_build_static.restype = i32
     lib.grca_set_ray_mask.argtypes = [P, i32, P, ctypes.c_int, P]
@@ -225,6 +228,15 @@ class Caster:
         if az is not None:
             self.set_azimuths(sid.value, az)
         return sid.value
+
+    def launch_config(self, ids, flags: int = 0) -> dict:
+        """The launch parameters a cast of these sensors with these flags would use."""
+        ids_a = np.ascontiguousarray(ids, dtype=np.int32)
+        out = np.zeros(4, np.int32)
+        self._check(self.lib.grca_get_launch_config(self.ctx, ids_a.ctypes.data, ids_a.shape[0], int(flags),
+                                                    out.ctypes.data), "grca_get_launch_config")
+        return {"inline_max": int(out[0]), "chunk_rays": int(out[1]), "cull_block": int(out[2]),
+                "cull_blocks_per_sm": int(out[3])}
 
     def build_static(self, n_static: int, stream=None):
         """Hybrid pipeline: static hierarchy over triangles [0, n_static) (0 drops it)."""

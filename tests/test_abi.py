@@ -60,6 +60,20 @@ def test_null_arguments_rejected_without_a_device(lib):
     assert lib.grca_cast(None, None, 0, None, None, 0, None) == -1
     lib.grca_get_stats.restype = ctypes.c_int32
     assert lib.grca_get_stats(None, None, None) == -1
+    P = ctypes.c_void_p
+    for name, argtypes, args in (
+            ("grca_get_launch_config", [P, P, ctypes.c_uint32, ctypes.c_uint32, P], (None, None, 1, 0, None)),
+            ("grca_build_static", [P, ctypes.c_uint32, P], (None, 0, None)),
+            ("grca_set_ray_mask", [P, ctypes.c_int32, P, ctypes.c_int, P], (None, 0, None, 0, None)),
+            ("grca_set_sensor_azimuths", [P, ctypes.c_int32, P], (None, 0, None)),
+            ("grca_set_range_noise", [P, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64], (None, 0, 0.1, 1)),
+            ("grca_upload_triangles", [P, P, ctypes.c_uint32, ctypes.c_int, P], (None, None, 0, 0, None)),
+            ("grca_update_vertices", [P, P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, P],
+             (None, None, 0, 0, 0, None))):
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int32
+        fn.argtypes = argtypes
+        assert fn(*args) == -1, name
 
 
 def test_struct_layouts_match_header():
