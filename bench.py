@@ -467,7 +467,7 @@ def main():
         "stats": {k: st_prof[k] for k in ("pairs", "survivors", "pairs_live", "candidates", "candidates_inline",
                                           "big_pairs",
                                           "chunks", "tests", "hits", "uncertain", "ties", "flagged_rays",
-                                          "recheck_pairs")},
+                                          "recheck_pairs", "group_culled", "bvh_node_visits", "bvh_tests")},
         "autotune_ms": tune_ms,
         "launch_config": launch_cfg,
         "static_build_s": build_s,
