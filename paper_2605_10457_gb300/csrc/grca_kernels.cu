@@ -1828,14 +1828,18 @@ __device__ unsigned long long test_fp64(const CastArgs& a, uint32_t g, uint32_t 
 }
 
 // R0: keep the queued pairs that can still beat or tie the ray's final FP32
-// winner (t_lo <= t_best (1 + beta)); flag their rays; drop the rest
+// winner (t_lo <= t_best (1 + beta)); flag their rays; drop the rest.  A kept
+// pair whose triangle is the ray's FP32 winner is flagged but not kept: R1
+// re-tests the winner of every flagged ray, so R2 would repeat that test.
 __global__ void k_recheck_filter(CastArgs a) {
     uint32_t np = min(*(volatile uint32_t*)&a.qcount[Q_RECHECK], a.recheck_cap);
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
         uint4 e = a.recheck[q];
-        float tbest = __uint_as_float((uint32_t)(a.keys[e.x] >> 32));
+        const unsigned long long kb = a.keys[e.x];
+        float tbest = __uint_as_float((uint32_t)(kb >> 32));
         if (__uint_as_float(e.z) <= __fmul_rn(tbest, 1.f + BETA)) {
             flag_ray(a, e.x);
+            if (e.y == (uint32_t)kb) a.recheck[q].y = NO_HIT;
         } else {
             a.recheck[q].y = NO_HIT;
         }
@@ -1854,19 +1858,47 @@ __global__ void k_recheck_rays(CastArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_FLAGGED] = *(volatile uint32_t*)&a.qcount[Q_FLAG];
 }
 
-// R2: FP64 re-test of every kept (ray, triangle) pair
-__global__ void k_recheck_pairs(CastArgs a) {
-    uint32_t np = min(*(volatile uint32_t*)&a.qcount[Q_RECHECK], a.recheck_cap);
-    uint32_t kept = 0;
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
-        uint4 pr = a.recheck[q];
-        if (pr.y == NO_HIT) continue;
-        kept++;
-        unsigned long long k = test_fp64(a, pr.x, pr.y);
-        if (k != KEY_MISS) atomicMin(&a.keys64[pr.x], k);
+constexpr int RECHECK_BLOCK = 256;
+
+// R2: FP64 re-test of every kept (ray, triangle) pair.  The FP64 pipe runs
+// at a small fraction of the FP32 rate, and a warp pays for a test however
+// few of its lanes take part, so each warp first compacts the kept pairs of
+// its slices of the queue into shared memory and tests them 32 at a time.
+__device__ __forceinline__ void recheck_pair(const CastArgs& a, uint2 pr) {
+    const unsigned long long k = test_fp64(a, pr.x, pr.y);
+    if (k != KEY_MISS) atomicMin(&a.keys64[pr.x], k);
+}
+__global__ void __launch_bounds__(RECHECK_BLOCK) k_recheck_pairs(CastArgs a) {
+    __shared__ uint2 buf[RECHECK_BLOCK / 32][64];
+    const uint32_t lane = threadIdx.x & 31u;
+    uint2* wb = buf[threadIdx.x >> 5];
+    const uint32_t np = min(*(volatile uint32_t*)&a.qcount[Q_RECHECK], a.recheck_cap);
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    uint32_t fill = 0, kept = 0;   // warp-uniform
+    for (uint32_t q0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; q0 < np; q0 += n_warps * 32u) {
+        const uint32_t q = q0 + lane;
+        uint2 pr = make_uint2(0u, NO_HIT);
+        if (q < np) {
+            const uint4 e = a.recheck[q];
+            pr = make_uint2(e.x, e.y);
+        }
+        const bool keep = pr.y != NO_HIT;
+        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) wb[fill + __popc(bal & ((1u << lane) - 1u))] = pr;   // fill < 32 here: index < 64
+        fill += __popc(bal);
+        __syncwarp();
+        if (fill >= 32u) {
+            recheck_pair(a, wb[lane]);
+            __syncwarp();
+            if (lane + 32u < fill) wb[lane] = wb[lane + 32u];
+            __syncwarp();
+            fill -= 32u;
+            kept += 32u;
+        }
     }
-    kept = __reduce_add_sync(0xffffffffu, kept);
-    if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&a.counters[C_RECHECK], (unsigned long long)kept);
+    if (lane < fill) recheck_pair(a, wb[lane]);
+    kept += fill;
+    if (lane == 0 && kept) atomicAdd(&a.counters[C_RECHECK], (unsigned long long)kept);
 }
 
 // output function of SplitMix64 (Steele, Lea and Flood, 2014) for state x
@@ -2199,7 +2231,7 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
         k_recheck_rays<<<n_sm * 2, 256, 0, st>>>(a);
         mark(K_RECHECK_RAYS, 1);
         mark(K_RECHECK_PAIRS, 0);
-        k_recheck_pairs<<<n_sm * 2, 256, 0, st>>>(a);
+        k_recheck_pairs<<<n_sm * 2, RECHECK_BLOCK, 0, st>>>(a);
         mark(K_RECHECK_PAIRS, 1);
         launches += 3;
     }
