@@ -142,7 +142,8 @@ typedef struct {
     uint64_t uncertain;       /* FP32 tests sent to the FP64 re-test */
     uint64_t ties;            /* tie events between FP32 hits on one ray */
     uint64_t flagged_rays;    /* rays resolved by the FP64 re-test */
-    uint64_t recheck_pairs;   /* queued (ray, triangle) pairs kept by the filter and re-tested in FP64 */
+    uint64_t recheck_pairs;   /* queued (ray, triangle) pairs kept by the filter and re-tested in FP64
+                                 (besides the re-test of each flagged ray's FP32 winner) */
     uint64_t group_culled;    /* pairs skipped whole by the group-level cull (GACP-T_g) */
     uint64_t bvh_node_visits; /* static-hierarchy node visits, one per warp of 32 rays (hybrid casts) */
     uint64_t bvh_tests;       /* ray-triangle pre-tests on static leaves (hybrid casts) */
