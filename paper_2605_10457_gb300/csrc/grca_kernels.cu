@@ -629,44 +629,52 @@ __device__ __forceinline__ bool elev_range_w(const SensorDev& S, const V3 w[3], 
     }
     smin = fminf(sv[0], fminf(sv[1], sv[2]));
     smax = fmaxf(sv[0], fmaxf(sv[1], sv[2]));
-    float dev = 0.f, ee_max = 0.f;
+    const float r2min = fminf(r2[0], fminf(r2[1], r2[2]));
+    const float r2max = fmaxf(r2[0], fmaxf(r2[1], r2[2]));
+    // upper bound of |w[k1]-w[k]|^2 from the world-frame edge E (sensor
+    // independent): |w[k1]-w[k]| <= |E|(1+u) + 4u|w|, so
+    // |w[k1]-w[k]|^2 <= 1.0001 |E|^2 + 1.6e5 (4u)^2 |w|^2 / 16; ee_max bounds all three
+    const float ee_max = 1.0001f * fmaxf(eeT[0], fmaxf(eeT[1], eeT[2])) + 5.7e-10f * r2max;
+    float dev = 0.f;
+    if (ee_max < 1e-4f * r2min && r2min > 1e-30f && r2min < 1e36f) {
+        // every edge is short (below): one bound for the three,
+        // 0.31 ee_max / r2min >= 0.31 ee / m2 of each edge
+        dev = 0.3100004f * __fdividef(ee_max, r2min);
+    } else {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        int k1 = k == 2 ? 0 : k + 1;
-        V3 a = w[k];
-        // upper bound of |w[k1]-w[k]|^2 from the world-frame edge E (sensor
-        // independent): |w[k1]-w[k]| <= |E|(1+u) + 4u|w|, so
-        // |w[k1]-w[k]|^2 <= 1.0001 |E|^2 + 1.6e5 (4u)^2 |w|^2 / 16
-        float m2 = fminf(r2[k], r2[k1]);
-        float ee = 1.0001f * eeT[k] + 5.7e-10f * fmaxf(r2[k], r2[k1]);
-        ee_max = fmaxf(ee_max, ee);
-        if (ee < 1e-4f * m2 && m2 > 1e-30f && m2 < 1e36f) {
-            // 0.31 ee / m2 with the fast division (2 ulp) rounded up by the constant;
-            // alpha <= 0.016 rad here, where the arc's rise stays below 0.3085 ee / m2
-            dev = fmaxf(dev, 0.3100004f * __fdividef(ee, m2));
-        } else {
-            V3 e = {w[k1].x - a.x, w[k1].y - a.y, w[k1].z - a.z};
-            ee = e.x * e.x + e.y * e.y + e.z * e.z;
-            // interior extremum of the edge's great circle: +-|m_h|/|m|, m = a x e
-            float ez = z[k1] - z[k];
-            float ae = a.x * e.x + a.y * e.y + a.z * e.z;
-            float num = z[k] * ae - ez * r2[k];
-            float den = ez * ae - z[k] * ee;
-            if (den < 0.f) {
-                num = -num;
-                den = -den;
-            }
-            if (den > 0.f && num > -1e-3f * den && num < 1.001f * den) {
-                V3 m = {a.y * e.z - a.z * e.y, a.z * e.x - a.x * e.z, a.x * e.y - a.y * e.x};
-                float mm = m.x * m.x + m.y * m.y + m.z * m.z;
-                float mz = u.x * m.x + u.y * m.y + u.z * m.z;
-                if (mm > 1e-12f * r2[k] * ee) {
-                    float v = sqrtf(fmaxf(mm - mz * mz, 0.f) * __frcp_rn(mm));
-                    float lam = fminf(fmaxf(num / den, 0.f), 1.f);
-                    float qz = z[k] + lam * ez;
-                    float tol = 1e-4f * sqrtf(r2[k] + ee);
-                    if (qz >= -tol) smax = fmaxf(smax, v);
-                    if (qz <= tol) smin = fminf(smin, -v);
+        for (int k = 0; k < 3; ++k) {
+            int k1 = k == 2 ? 0 : k + 1;
+            V3 a = w[k];
+            float m2 = fminf(r2[k], r2[k1]);
+            float ee = 1.0001f * eeT[k] + 5.7e-10f * fmaxf(r2[k], r2[k1]);
+            if (ee < 1e-4f * m2 && m2 > 1e-30f && m2 < 1e36f) {
+                // 0.31 ee / m2 with the fast division (2 ulp) rounded up by the constant;
+                // alpha <= 0.016 rad here, where the arc's rise stays below 0.3085 ee / m2
+                dev = fmaxf(dev, 0.3100004f * __fdividef(ee, m2));
+            } else {
+                V3 e = {w[k1].x - a.x, w[k1].y - a.y, w[k1].z - a.z};
+                ee = e.x * e.x + e.y * e.y + e.z * e.z;
+                // interior extremum of the edge's great circle: +-|m_h|/|m|, m = a x e
+                float ez = z[k1] - z[k];
+                float ae = a.x * e.x + a.y * e.y + a.z * e.z;
+                float num = z[k] * ae - ez * r2[k];
+                float den = ez * ae - z[k] * ee;
+                if (den < 0.f) {
+                    num = -num;
+                    den = -den;
+                }
+                if (den > 0.f && num > -1e-3f * den && num < 1.001f * den) {
+                    V3 m = {a.y * e.z - a.z * e.y, a.z * e.x - a.x * e.z, a.x * e.y - a.y * e.x};
+                    float mm = m.x * m.x + m.y * m.y + m.z * m.z;
+                    float mz = u.x * m.x + u.y * m.y + u.z * m.z;
+                    if (mm > 1e-12f * r2[k] * ee) {
+                        float v = sqrtf(fmaxf(mm - mz * mz, 0.f) * __frcp_rn(mm));
+                        float lam = fminf(fmaxf(num / den, 0.f), 1.f);
+                        float qz = z[k] + lam * ez;
+                        float tol = 1e-4f * sqrtf(r2[k] + ee);
+                        if (qz >= -tol) smax = fmaxf(smax, v);
+                        if (qz <= tol) smin = fminf(smin, -v);
+                    }
                 }
             }
         }
@@ -674,7 +682,6 @@ __device__ __forceinline__ bool elev_range_w(const SensorDev& S, const V3 w[3], 
     smin -= dev;
     smax += dev;
     float h2min = fminf(r2[0] - z[0] * z[0], fminf(r2[1] - z[1] * z[1], r2[2] - z[2] * z[2]));
-    float r2max = fmaxf(r2[0], fmaxf(r2[1], r2[2]));
     bool pierced = false;
     if (h2min <= 1.01f * ee_max + 8.f * U32 * r2max) {
         V3 p[3] = {rotB(S.B, w[0]), rotB(S.B, w[1]), rotB(S.B, w[2])};
