@@ -89,9 +89,15 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                       "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+        # the timed region starts once the sampler runs (its first sample is out)
+        t_end = time.time() + 3.0
+        while self.p is not None and time.time() < t_end and self.p.poll() is None:
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.01)
 
     def stop(self) -> dict:
         if self.p is None:
@@ -191,7 +197,9 @@ def run_reference(args):
     from grading import stratified_rays
     orc = oracle.Oracle(sc.sensors)
     threads = os.cpu_count() or 1
-    per_step = args.ref_rays
+    # about a second of oracle work per step on 16 cores; long runs take fewer
+    # rays per step so that the whole run stays within a few minutes
+    per_step = args.ref_rays or max(8, min(48, 2400 // max(1, args.steps + args.warmup)))
     times = []
     for step in range(args.warmup + args.steps):
         rays = stratified_rays(sc.sensors, max(1, per_step // len(sc.sensors)), seed=100 + step)[:per_step]
@@ -221,14 +229,15 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c5")
     ap.add_argument("--frames", type=int, default=8, help="distinct animated frames kept on the device")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
-    ap.add_argument("--ref-rays", type=int, default=48, help="rays per step of the reference arm")
+    ap.add_argument("--ref-rays", type=int, default=None,
+                    help="rays per step of the reference arm (default: 48, fewer for long runs)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="default: steps")
     ap.add_argument("--stats", action="store_true", help="print cast statistics to stderr")
     ap.add_argument("--capacity", default="large", choices=["large", "small"],
