@@ -202,9 +202,11 @@ grca_status grca_cast_host(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_
                            uint32_t first_dynamic, uint32_t n_dynamic, float* out_dist_host,
                            uint32_t* out_tri_host, uint32_t flags, void* stream);
 
-/* Time the launch-parameter candidates (culling block shape, inline
- * candidate limit, chunk size) on the current scene for these sensors and
- * flags, and keep the fastest for later casts of the same shape.  Runs casts
+/* Time the launch-parameter candidates (culling block shape: 128 or 256
+ * threads, 2 to 32 blocks per SM; inline candidate limit 4 to 1024; chunk
+ * size 32 to 256 rays) by coordinate descent on the current scene for these
+ * sensors and flags, and keep the fastest for later casts of the same shape.
+ * The result does not depend on these parameters.  Runs casts
  * into the given output buffers; synchronous.  *out_ms (nullable) receives
  * the best frame time. */
 grca_status grca_autotune(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_sensors, float* out_dist,

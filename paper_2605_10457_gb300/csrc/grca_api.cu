@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <new>
 #include <string>
@@ -832,8 +833,12 @@ static LaunchCfg cfg_for(grca_ctx* ctx, const CastArgs& a) {
 // split_at > 0: launch the key init and the elevation cull of [tri_first,
 // split_at) first, wait for `ready` (the copy of the rest), then the rest of
 // the frame (graph-replayed when use_graph)
+// split_at > 0: part 1 of the frame (key init and the elevation cull of
+// triangles below split_at) runs now, then `st` waits for `ready`, then
+// `between` (if any) and part 2 are enqueued
 static grca_status run_frame(grca_ctx* ctx, CastArgs& a, const LaunchCfg& cfg, cudaStream_t st, bool use_graph,
-                             uint32_t split_at = 0, cudaEvent_t ready = nullptr) {
+                             uint32_t split_at = 0, cudaEvent_t ready = nullptr,
+                             const std::function<void()>& between = nullptr) {
     a.inline_max = (uint32_t)cfg.inline_max;
     a.chunk_rays = (uint32_t)cfg.chunk_rays;
     uint32_t pending = ctx->pending_launches;
@@ -847,6 +852,7 @@ static grca_status run_frame(grca_ctx* ctx, CastArgs& a, const LaunchCfg& cfg, c
         pending += (uint32_t)launch_frame(a, cfg, ctx->n_sm, st, ctx->profiling ? &mk : nullptr, part1);
         CK(cudaGetLastError());
         CK(cudaStreamWaitEvent(st, ready, 0));
+        if (between) between();
         part2.part = 2;
         part2.at = split_at;
     }
@@ -951,6 +957,9 @@ grca_status grca_cast_host(grca_ctx* ctx, const int32_t* ids, uint32_t n, const 
         CK(cudaMemcpyAsync(ctx->d_tris + 9ull * first_dyn, xyz_dyn, sizeof(float) * 9ull * n_dyn,
                            cudaMemcpyHostToDevice, ctx->copy_stream));
         CK(cudaEventRecord(ctx->ev_copied, ctx->copy_stream));
+        // group boxes of the static head are current unless a stale range
+        // from earlier updates reaches below the tail
+        const bool head_boxes_current = ctx->gb_hi <= ctx->gb_lo || ctx->gb_lo >= first_dyn;
         if (ctx->gb_hi <= ctx->gb_lo) {
             ctx->gb_lo = first_dyn;
             ctx->gb_hi = first_dyn + n_dyn;
@@ -967,7 +976,17 @@ grca_status grca_cast_host(grca_ctx* ctx, const int32_t* ids, uint32_t n, const 
             return rs;
         }
         ctx->last_n_rays = a.n_rays_total;
-        if (a.gbounds || a.bvh_nodes) {
+        if (a.gbounds && !a.bvh_nodes && head_boxes_current) {
+            // the static head is culled by its (unchanged) group boxes while the
+            // tail is copied; the tail's boxes, including a group that straddles
+            // the split, are refreshed once the copy is in.  Part 1 reads only
+            // static triangles of a straddling group, which its old box bounds.
+            const uint32_t lo = ctx->gb_lo, hi = ctx->gb_hi;
+            ctx->gb_lo = ctx->gb_hi = 0;
+            ctx->pending_launches++;   // the group-bound kernel enqueued between the parts
+            rs = run_frame(ctx, a, cfg_for(ctx, a), st, (flags & GRCA_CAST_GRAPH) != 0, first_dyn, ctx->ev_copied,
+                           [&]() { launch_group_bounds(ctx->d_tris, ctx->n_tris, lo, hi - lo, ctx->d_gb, ctx->n_sm, st); });
+        } else if (a.gbounds || a.bvh_nodes) {
             // group boxes (and the hierarchy split) need the new vertices first
             CK(cudaStreamWaitEvent(st, ctx->ev_copied, 0));
             if (a.gbounds && ctx->gb_hi > ctx->gb_lo) {
@@ -1112,10 +1131,10 @@ grca_status grca_autotune(grca_ctx* ctx, const int32_t* ids, uint32_t n, float* 
     float best_ms;
     rs = time_cfg(best, best_ms);
     // coordinate descent over the launch parameters
-    const int inl[] = {4, 8, 16, 32, 64, 128};
+    const int inl[] = {4, 8, 16, 32, 64, 128, 256, 512, 1024};
     const int chk[] = {32, 64, 128, 256};
     const int blk[] = {128, 256};
-    const int bps[] = {2, 4, 8};
+    const int bps[] = {2, 4, 8, 16, 32};
     for (int pass = 0; pass < 2 && rs == GRCA_OK; ++pass) {
         for (int v : inl) {
             LaunchCfg c = best;

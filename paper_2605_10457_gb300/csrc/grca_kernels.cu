@@ -2221,7 +2221,10 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
     if (a.bvh_nodes) {
         // static side of a hybrid cast, after the dynamic triangles so that
         // their hits bound the traversal
-        const int blocks = (int)std::min<uint32_t>((a.n_rays_total + BVH_BLOCK - 1) / BVH_BLOCK, (uint32_t)n_sm * 16);
+        // many more blocks than fit at once: the fans differ widely in cost, and
+        // blocks that finish early make room for the next ones (64 per SM measured
+        // 11 % faster than 16 on c5; one fan per warp was slower again)
+        const int blocks = (int)std::min<uint32_t>((a.n_rays_total + BVH_BLOCK - 1) / BVH_BLOCK, (uint32_t)n_sm * 64);
         mark(K_BVH, 0);
         if (recheck)
             k_bvh<true><<<std::max(blocks, 1), BVH_BLOCK, 0, st>>>(a);
