@@ -1336,8 +1336,120 @@ struct CullBWarpSmem {
     uint32_t tri[32];            // per pair: triangle id
     float inv[32];               // per pair: rounded-up 1 / ray count
     uint32_t own[32];            // lane of the pair with the r-th candidate run (r-th set bit of the owner mask)
+    uint4 pend[64];              // live pairs waiting for their setup: triangle, meta, first ray, candidates
     uint32_t cnt[8];             // live, cand, inl, big, tests, hits, unc, ties
 };
+
+// Setup, first test and cooperative candidate expansion of the warp's
+// pending live pairs W.pend[0, np), np <= 32, one pair per lane.  Called by
+// the whole warp.
+template <bool RECHECK>
+__device__ __forceinline__ void cull_b_test_pairs(const CastArgs& a, const CullSmem& M, CullBWarpSmem& W, uint32_t np,
+                                                  uint32_t lane, bool dump, uint32_t& c_hits, uint32_t& c_unc,
+                                                  uint32_t& c_ties) {
+    uint32_t ncand = 0, hit0 = 0, tested0 = 0;
+    if (lane < np) {
+        const uint4 e = W.pend[lane];
+        const uint32_t tri = e.x, meta = e.y, my_r0 = e.z, nc = e.w;
+        const uint32_t sn = meta >> 26, j_lo = meta & 1023u;
+        const SensorDev& S = M.sens[sn];
+        float t9[9];
+        const float* src = a.tris + 9ull * tri;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) t9[k] = __ldg(src + k);
+        TriW T;
+        tri_world(t9, T);
+        V3 w[3], p[3];
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+            w[kk] = rel_origin(S, T.v[kk]);
+            p[kk] = rotB(S.B, w[kk]);
+        }
+        const float det = vdot(w[0], T.n);
+        const float err_det = det_error(w[0], T);
+        const bool det_unc = fabsf(det) <= err_det;
+        if (det != 0.f || (RECHECK && det_unc)) {
+            make_setup(S, T, w, p, det, err_det, SetupWriterSoA{&W.st[0][0], lane});
+            W.tri[lane] = tri;
+            W.meta[lane] = meta;
+            W.r0[lane] = my_r0;
+            W.inv[lane] = __frcp_ru((float)((meta >> 10) & 0xFFFFu));
+            // the pair's first candidate is tested here by its own lane;
+            // the remaining ones are expanded cooperatively below
+            const uint32_t g = S.ray_off + j_lo * S.n_rays + my_r0;
+            const unsigned long long cur = __ldcg(&a.keys[g]);
+            V3 d = ray_dir(M.ch[S.ch_loc + j_lo], __ldg(&a.az_sc[S.az_off + my_r0]));
+            float t, terr;
+            int res = test_fp32<RECHECK>(SetupSoA{&W.st[0][0], lane}, S, d, t, terr);
+            if (dump) dump_candidate(a, g, tri);
+            hit0 = commit_pre<RECHECK>(a, g, tri, res, t, terr, cur, c_unc, c_ties);
+            tested0 = 1;
+            ncand = nc - 1;
+        }
+    }
+    // warp prefix sum of the inline candidate counts
+    uint32_t incl = ncand;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((int)lane >= o) incl += t;
+    }
+    const uint32_t excl = incl - ncand;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t nz = __ballot_sync(0xffffffffu, ncand > 0);   // lanes that own candidates, in order
+    if (ncand > 0) W.own[__popc(nz & ((1u << lane) - 1u))] = lane;
+    {
+        const uint32_t s_t0 = __reduce_add_sync(0xffffffffu, tested0), s_h0 = __reduce_add_sync(0xffffffffu, hit0);
+        if (lane == 0) {
+            W.cnt[2] += total + s_t0;
+            W.cnt[4] += total + s_t0;
+            W.cnt[5] += s_h0;
+        }
+    }
+    __syncwarp();
+    for (uint32_t c0 = 0; c0 < total; c0 += 32) {
+        // rank (among owning lanes) of the pair holding candidate c0, and the
+        // pairs that start inside this round of 32 candidates
+        const uint32_t base_rank = __popc(__ballot_sync(0xffffffffu, ncand > 0 && incl <= c0));
+        const uint32_t starts =
+            __reduce_or_sync(0xffffffffu, (ncand > 0 && excl > c0 && excl < c0 + 32) ? (1u << (excl - c0)) : 0u);
+        const uint32_t rank = base_rank + __popc(starts & ((2u << lane) - 2u));
+        const uint32_t own = W.own[min(rank, 31u)];
+        const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, own & 31u);
+        const uint32_t meta = W.meta[own & 31u];
+        const uint32_t r0o = W.r0[own & 31u];
+        const uint32_t tri = W.tri[own & 31u];
+        const float inv = W.inv[own & 31u];
+        const uint32_t cc = c0 + lane;
+        if (cc < total) {
+            const uint32_t nr = (meta >> 10) & 0xFFFFu;
+            const uint32_t sn = meta >> 26;
+            uint32_t idx = cc - o_excl + 1;   // candidate 0 was tested by the owner lane
+            // quotient from the rounded-up reciprocal, then one correction
+            // step in each direction (idx < 2^24, so (float)idx is exact)
+            uint32_t jo = (uint32_t)((float)idx * inv);
+            if (jo * nr > idx) --jo;
+            uint32_t io = idx - jo * nr;
+            if (io >= nr) {
+                ++jo;
+                io -= nr;
+            }
+            const SensorDev& S = M.sens[sn];
+            const uint32_t j = (meta & 1023u) + jo;
+            uint32_t i = r0o + io;
+            if (i >= S.n_rays) i -= S.n_rays;
+            const uint32_t g = S.ray_off + j * S.n_rays + i;
+            const unsigned long long cur = __ldcg(&a.keys[g]);   // issued before the test arithmetic
+            V3 d = ray_dir(M.ch[S.ch_loc + j], __ldg(&a.az_sc[S.az_off + i]));
+            float t, terr;
+            int res = test_fp32<RECHECK>(SetupSoA{&W.st[0][0], own & 31u}, S, d, t, terr);
+            if (dump) dump_candidate(a, g, tri);
+            c_hits += commit_pre<RECHECK>(a, g, tri, res, t, terr, cur, c_unc, c_ties);
+        }
+    }
+    __syncwarp();
+}
+
 template <bool RECHECK, bool BRUTE>
 __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1346,6 +1458,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
     CullBWarpSmem& W = reinterpret_cast<CullBWarpSmem*>(M.rest)[wib];
     const bool dump = a.flags & 16u;
     if (lane < 8) W.cnt[lane] = 0;
+    __syncwarp();
     uint32_t c_unc = 0, c_ties = 0, c_hits = 0;
     const uint32_t n = min(*(volatile uint32_t*)&a.qcount[Q_SURV], a.surv_cap);
     // part 1 records how far it goes; part 2 starts there (a.surv_part)
@@ -1353,10 +1466,16 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
     if (a.surv_part == 1 && blockIdx.x == 0 && threadIdx.x == 0) a.qcount[Q_SURV_SPLIT] = n;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t gwarp = ((blockIdx.x * blockDim.x) >> 5) + wib;
+    // Live pairs with small spans queue up in W.pend and get their setups 32
+    // at a time, so that the setup and the tests run with full warps even
+    // where the azimuth cull or the deferred queue took many of a batch's
+    // survivors (warp-uniform count)
+    uint32_t fill = 0;
     for (uint32_t b0 = s0 + gwarp * 32; b0 < n; b0 += n_warps * 32) {
         const uint32_t q = b0 + lane;
-        uint32_t ncand = 0;
-        uint32_t l_live = 0, l_cand = 0, l_big = 0, hit0 = 0, tested0 = 0;
+        uint32_t l_live = 0, l_cand = 0, l_big = 0;
+        bool pend_me = false;
+        uint4 pe = make_uint4(0u, 0u, 0u, 0u);
         if (q < n) {
             const unsigned long long r = __ldcs(&a.surv[q]);
             const uint32_t tri = (uint32_t)r, span = (uint32_t)(r >> 32) & 0x1FFFFFu, sn = (uint32_t)(r >> 53);
@@ -1440,100 +1559,33 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
                     }
                     l_big = 1;
                 } else {
-                    TriW T;
-                    tri_world(t9, T);
-                    float det = vdot(w[0], T.n);
-                    float err_det = det_error(w[0], T);
-                    bool det_unc = fabsf(det) <= err_det;
-                    if (det != 0.f || (RECHECK && det_unc)) {
-                        make_setup(S, T, w, p, det, err_det, SetupWriterSoA{&W.st[0][0], lane});
-                        const uint32_t my_r0 = (uint32_t)imod(sp.u_lo, (int)S.n_rays);
-                        W.tri[lane] = tri;
-                        W.meta[lane] = (uint32_t)sp.j_lo | ((uint32_t)sp.n_r << 10) | (sn << 26);
-                        W.r0[lane] = my_r0;
-                        W.inv[lane] = __frcp_ru((float)sp.n_r);
-                        // the pair's first candidate is tested here by its own lane;
-                        // the remaining ones are expanded cooperatively below
-                        const uint32_t g = S.ray_off + (uint32_t)sp.j_lo * S.n_rays + my_r0;
-                        const unsigned long long cur = __ldcg(&a.keys[g]);
-                        V3 d = ray_dir(M.ch[S.ch_loc + sp.j_lo], __ldg(&a.az_sc[S.az_off + my_r0]));
-                        float t, terr;
-                        int res = test_fp32<RECHECK>(SetupSoA{&W.st[0][0], lane}, S, d, t, terr);
-                        if (dump) dump_candidate(a, g, tri);
-                        hit0 = commit_pre<RECHECK>(a, g, tri, res, t, terr, cur, c_unc, c_ties);
-                        tested0 = 1;
-                        ncand = nc - 1;
-                    }
+                    pend_me = true;
+                    pe = make_uint4(tri, (uint32_t)sp.j_lo | ((uint32_t)sp.n_r << 10) | (sn << 26),
+                                    (uint32_t)imod(sp.u_lo, (int)S.n_rays), nc);
                 }
             }
         }
-        // warp prefix sum of the inline candidate counts
-        uint32_t incl = ncand;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if ((int)lane >= o) incl += t;
-        }
-        const uint32_t excl = incl - ncand;
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        const uint32_t nz = __ballot_sync(0xffffffffu, ncand > 0);   // lanes that own candidates, in order
-        if (ncand > 0) W.own[__popc(nz & ((1u << lane) - 1u))] = lane;
+        const uint32_t bal = __ballot_sync(0xffffffffu, pend_me);
+        if (pend_me) W.pend[fill + __popc(bal & ((1u << lane) - 1u))] = pe;   // fill < 32 here: index < 64
+        fill += __popc(bal);
         {
             const uint32_t s_live = __reduce_add_sync(0xffffffffu, l_live), s_cand = __reduce_add_sync(0xffffffffu, l_cand),
-                           s_big = __reduce_add_sync(0xffffffffu, l_big), s_t0 = __reduce_add_sync(0xffffffffu, tested0),
-                           s_h0 = __reduce_add_sync(0xffffffffu, hit0);
+                           s_big = __reduce_add_sync(0xffffffffu, l_big);
             if (lane == 0) {
                 W.cnt[0] += s_live;
                 W.cnt[1] += s_cand;
-                W.cnt[2] += total + s_t0;
                 W.cnt[3] += s_big;
-                W.cnt[4] += total + s_t0;
-                W.cnt[5] += s_h0;
             }
         }
         __syncwarp();
-        for (uint32_t c0 = 0; c0 < total; c0 += 32) {
-            // rank (among owning lanes) of the pair holding candidate c0, and the
-            // pairs that start inside this round of 32 candidates
-            const uint32_t base_rank = __popc(__ballot_sync(0xffffffffu, ncand > 0 && incl <= c0));
-            const uint32_t starts =
-                __reduce_or_sync(0xffffffffu, (ncand > 0 && excl > c0 && excl < c0 + 32) ? (1u << (excl - c0)) : 0u);
-            const uint32_t rank = base_rank + __popc(starts & ((2u << lane) - 2u));
-            const uint32_t own = W.own[min(rank, 31u)];
-            const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, own & 31u);
-            const uint32_t meta = W.meta[own & 31u];
-            const uint32_t r0o = W.r0[own & 31u];
-            const uint32_t tri = W.tri[own & 31u];
-            const float inv = W.inv[own & 31u];
-            const uint32_t cc = c0 + lane;
-            if (cc < total) {
-                const uint32_t nr = (meta >> 10) & 0xFFFFu;
-                const uint32_t sn = meta >> 26;
-                uint32_t idx = cc - o_excl + 1;   // candidate 0 was tested by the owner lane
-                // quotient from the rounded-up reciprocal, then one correction
-                // step in each direction (idx < 2^24, so (float)idx is exact)
-                uint32_t jo = (uint32_t)((float)idx * inv);
-                if (jo * nr > idx) --jo;
-                uint32_t io = idx - jo * nr;
-                if (io >= nr) {
-                    ++jo;
-                    io -= nr;
-                }
-                const SensorDev& S = M.sens[sn];
-                const uint32_t j = (meta & 1023u) + jo;
-                uint32_t i = r0o + io;
-                if (i >= S.n_rays) i -= S.n_rays;
-                const uint32_t g = S.ray_off + j * S.n_rays + i;
-                const unsigned long long cur = __ldcg(&a.keys[g]);   // issued before the test arithmetic
-                V3 d = ray_dir(M.ch[S.ch_loc + j], __ldg(&a.az_sc[S.az_off + i]));
-                float t, terr;
-                int res = test_fp32<RECHECK>(SetupSoA{&W.st[0][0], own & 31u}, S, d, t, terr);
-                if (dump) dump_candidate(a, g, tri);
-                c_hits += commit_pre<RECHECK>(a, g, tri, res, t, terr, cur, c_unc, c_ties);
-            }
+        if (fill >= 32u) {
+            cull_b_test_pairs<RECHECK>(a, M, W, 32u, lane, dump, c_hits, c_unc, c_ties);
+            if (lane + 32u < fill) W.pend[lane] = W.pend[lane + 32u];
+            __syncwarp();
+            fill -= 32u;
         }
-        __syncwarp();
     }
+    if (fill > 0u) cull_b_test_pairs<RECHECK>(a, M, W, fill, lane, dump, c_hits, c_unc, c_ties);
     c_unc = __reduce_add_sync(0xffffffffu, c_unc);
     c_ties = __reduce_add_sync(0xffffffffu, c_ties);
     c_hits = __reduce_add_sync(0xffffffffu, c_hits);
