@@ -1323,11 +1323,13 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
 
 // ---------------------------------------------------------------------------
 // k_cull_b: phase B over the survivor queue, warp-cooperative.  Each warp
-// takes 32 survivors: (1) per lane, range cull and azimuth span; large spans
-// go to the deferred queue; (2) per lane with a small live span, the test
-// setup into shared memory; (3) the warp expands all candidates of its 32
-// pairs together, one candidate per lane (owner found by binary search over
-// the warp's prefix sums), so the tests run without lane divergence.
+// takes 32 survivors at a time: (1) per lane, range cull and azimuth span;
+// large spans go to the deferred queue, small live spans to the warp's list
+// of pending pairs; (2) once 32 pairs are pending, one per lane gets its test
+// setup into shared memory and its first candidate tested; (3) the warp
+// expands all other candidates of those 32 pairs together, one candidate per
+// lane (owner found from the warp's prefix sums), so the setups and tests run
+// with full warps and without lane divergence.
 // ---------------------------------------------------------------------------
 struct CullBWarpSmem {
     float st[SETUP_FIELDS][32];  // field-major setups of the warp's 32 pairs
