@@ -972,7 +972,8 @@ grca_status grca_cast_host(grca_ctx* ctx, const int32_t* ids, uint32_t n, const 
         rs = prepare_cast(ctx, ids, n, ctx->d_out_dist, ctx->d_out_tri, flags, st, a);
         ctx->defer_bounds = false;
         if (rs != GRCA_OK) {
-            cudaStreamWaitEvent(st, ctx->ev_copied, 0);
+            // the caller may reuse its host buffer once this call returns
+            cudaStreamSynchronize(ctx->copy_stream);
             return rs;
         }
         ctx->last_n_rays = a.n_rays_total;
@@ -1003,7 +1004,10 @@ grca_status grca_cast_host(grca_ctx* ctx, const int32_t* ids, uint32_t n, const 
     } else {
         rs = grca_cast(ctx, ids, n, ctx->d_out_dist, ctx->d_out_tri, flags, stream);
     }
-    if (rs != GRCA_OK) return rs;
+    if (rs != GRCA_OK) {
+        if (overlap) cudaStreamSynchronize(ctx->copy_stream);   // the host source stays in use until then
+        return rs;
+    }
     CK(cudaMemcpyAsync(out_dist_h, ctx->d_out_dist, sizeof(float) * total, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(out_tri_h, ctx->d_out_tri, sizeof(uint32_t) * total, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
