@@ -52,11 +52,12 @@ def kernels_digest() -> str:
     return h.hexdigest()
 
 
-def measured_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary
-    (profiles/traffic_c5.json), or None when the kernel sources changed since."""
+def measured_traffic(kernel: str, workload: str = "c5"):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of
+    this workload (profiles/traffic_<workload>.json), or None when there is
+    none or the kernel sources changed since the capture."""
     try:
-        d = json.load(open(os.path.join(ROOT, "profiles", "traffic_c5.json")))
+        d = json.load(open(os.path.join(ROOT, "profiles", f"traffic_{workload}.json")))
     except (OSError, ValueError):
         return None
     e = d.get("kernels", {}).get(kernel)
@@ -407,6 +408,8 @@ def main():
 
     # --- roofline of the dominant kernel ---------------------------------------
     peaks, src = _peaks()
+    # the committed DRAM counters belong to one workload (c5, unlimited range)
+    traffic_key = args.config if args.d_max is None else f"{args.config}_dmax{args.d_max:g}"
     dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
     dom_name, dom_v = dom
     avg_ms = dom_v["total_ms"] / max(1, dom_v["launches"])
@@ -426,7 +429,7 @@ def main():
     ka = prof.get("k_cull_a", {"total_ms": 1.0, "launches": 1})
     hbm_achieved = (sc.n_tris * TRI_BYTES) / (ka["total_ms"] / max(1, ka["launches"]) / 1e3) / 1e9
     roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak if fp32_peak else None, "traffic": measured_traffic(dom_name),
+                "frac": achieved / fp32_peak if fp32_peak else None, "traffic": measured_traffic(dom_name, traffic_key),
                 "peak_source": f"FP32 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (unit counts and max clock)",
                 "algorithmic": {"k_cull_a": f"{F_CULL_A:.0f} flop per (tri, sensor) pair",
                                 "k_cull_b": f"{F_CULL_B:.0f} flop per surviving pair + {F_SETUP:.0f} per live pair "
