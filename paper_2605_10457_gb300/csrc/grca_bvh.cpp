@@ -44,8 +44,8 @@ struct Box {
     }
 };
 
-constexpr int BINS = 16;
-constexpr uint32_t LEAF_TARGET = 4;     // SAH may stop at or below this many triangles
+constexpr int BINS = 32;
+constexpr uint32_t LEAF_TARGET = 2;     // SAH may stop at or below this many triangles
 constexpr int MEDIAN_DEPTH = 40;        // beyond this depth, split at the median
 constexpr uint32_t PAR_MIN = 1u << 18;  // subtrees at least this large build in their own thread
 constexpr int PAR_DEPTH = 4;            // ... down to this depth (up to 16 threads)
