@@ -85,7 +85,16 @@ enum {
     GRCA_CAST_NO_GROUP_CULL = 1u << 6,
     /* Trace the static triangles through the culls even when a static
      * hierarchy exists (grca_build_static): for A/B timing and debugging. */
-    GRCA_CAST_NO_STATIC_BVH = 1u << 7
+    GRCA_CAST_NO_STATIC_BVH = 1u << 7,
+    /* grca_cast_host only (other calls reject it): return once the frame is
+     * enqueued instead of once its results are on the host.  The results are
+     * copied to the host arrays on a stream of the context's own, after the
+     * frame; grca_host_wait tells when they are there.  Until then the host
+     * arrays must not be read and the host source `xyz_dynamic` must stay
+     * unchanged.  The next frame on the context runs meanwhile (only its key
+     * decode waits for this copy-out), so a caller that alternates two pairs
+     * of host arrays overlaps each frame's copy-out with the next frame. */
+    GRCA_CAST_HOST_ASYNC = 1u << 8
 };
 
 /* Context options (all fields 0 = library default). */
@@ -193,7 +202,8 @@ grca_status grca_cast(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_senso
  * (`xyz_dynamic`, n_dynamic triangles starting at first_dynamic, HOST;
  * pinned memory gives the fastest copy) are copied in, the results copied
  * back into the host arrays, and the call returns once they are there
- * (end-to-end frame).  When the dynamic triangles are the tail of the set
+ * (end-to-end frame; with GRCA_CAST_HOST_ASYNC, once the frame is enqueued).
+ * When the dynamic triangles are the tail of the set
  * (first_dynamic + n_dynamic = uploaded count, first_dynamic > 0), their copy
  * runs on an internal stream while the elevation cull works through the
  * triangles before them.  Returns GRCA_ERR_INVALID_ARG for a range outside
@@ -201,6 +211,13 @@ grca_status grca_cast(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_senso
 grca_status grca_cast_host(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_sensors, const float* xyz_dynamic,
                            uint32_t first_dynamic, uint32_t n_dynamic, float* out_dist_host,
                            uint32_t* out_tri_host, uint32_t flags, void* stream);
+
+/* Block until at most `max_pending` grca_cast_host calls with
+ * GRCA_CAST_HOST_ASYNC still have results on their way to the host (0: all
+ * of them are there); casts complete in call order.  At most 8 such casts
+ * are in flight: a ninth call first waits for the oldest.  Returns
+ * GRCA_ERR_CUDA if a copy failed, GRCA_ERR_INVALID_ARG for a null context. */
+grca_status grca_host_wait(grca_ctx* ctx, uint32_t max_pending);
 
 /* Time the launch-parameter candidates (culling block shape: 128 or 256
  * threads, 2 to 32 blocks per SM; inline candidate limit 4 to 1024; chunk

@@ -76,6 +76,13 @@ struct grca_ctx {
     // cull of the static triangles (grca_cast_host)
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_free = nullptr, ev_copied = nullptr;
+    // asynchronous host casts: results go out on d2h_stream; ev_out holds, in
+    // order, one event per cast whose copy-out may still be running
+    static constexpr int OUT_RING = 8;
+    cudaStream_t d2h_stream = nullptr;
+    cudaEvent_t ev_decoded = nullptr;
+    cudaEvent_t ev_out[OUT_RING] = {};
+    uint32_t out_head = 0, out_count = 0;
     bool defer_bounds = false;  // prepare_cast leaves the group-box refresh to the caller
 
     float* d_tris = nullptr;
@@ -285,6 +292,13 @@ grca_status grca_create(grca_ctx** out, int device, const grca_options* opt) {
         fail(e, "cudaEventCreate");
     if (st == GRCA_OK && (e = cudaEventCreateWithFlags(&ctx->ev_copied, cudaEventDisableTiming)) != cudaSuccess)
         fail(e, "cudaEventCreate");
+    if (st == GRCA_OK && (e = cudaStreamCreateWithFlags(&ctx->d2h_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        fail(e, "cudaStreamCreate");
+    if (st == GRCA_OK && (e = cudaEventCreateWithFlags(&ctx->ev_decoded, cudaEventDisableTiming)) != cudaSuccess)
+        fail(e, "cudaEventCreate");
+    for (int k = 0; k < grca_ctx::OUT_RING && st == GRCA_OK; ++k)
+        if ((e = cudaEventCreateWithFlags(&ctx->ev_out[k], cudaEventDisableTiming)) != cudaSuccess)
+            fail(e, "cudaEventCreate");
     if (st == GRCA_OK && (e = cudaMalloc(&ctx->d_big, sizeof(BigPair) * o.big_pair_capacity)) != cudaSuccess)
         fail(e, "cudaMalloc(big)");
     if (st == GRCA_OK && (e = cudaMalloc(&ctx->d_setups, sizeof(PairSetup) * o.big_pair_capacity)) != cudaSuccess)
@@ -326,6 +340,7 @@ void grca_destroy(grca_ctx* ctx) {
     DeviceGuard g(ctx->device);
     if (ctx->cap_stream) cudaStreamSynchronize(ctx->cap_stream);
     if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+    if (ctx->d2h_stream) cudaStreamSynchronize(ctx->d2h_stream);
     cudaDeviceSynchronize();
     free_graphs(ctx);
     for (SensorHost& sh : ctx->sensors) cudaFree(sh.d_mask);
@@ -362,6 +377,10 @@ void grca_destroy(grca_ctx* ctx) {
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->ev_free) cudaEventDestroy(ctx->ev_free);
     if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
+    if (ctx->d2h_stream) cudaStreamDestroy(ctx->d2h_stream);
+    if (ctx->ev_decoded) cudaEventDestroy(ctx->ev_decoded);
+    for (cudaEvent_t ev : ctx->ev_out)
+        if (ev) cudaEventDestroy(ev);
     delete ctx;
 }
 
@@ -921,6 +940,15 @@ grca_status grca_cast_host(grca_ctx* ctx, const int32_t* ids, uint32_t n, const 
     if (!ctx || !out_dist_h || !out_tri_h || (!xyz_dyn && n_dyn)) return GRCA_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
+    const bool async_out = flags & GRCA_CAST_HOST_ASYNC;
+    flags &= ~(uint32_t)GRCA_CAST_HOST_ASYNC;
+    // the copy-out of an earlier asynchronous cast may still read the device
+    // result buffers: this frame's decode waits for it (d2h_stream is in order,
+    // so the latest copy-out covers the earlier ones)
+    auto wait_prev_out = [&]() {
+        if (ctx->out_count)
+            cudaStreamWaitEvent(st, ctx->ev_out[(ctx->out_head + ctx->out_count - 1) % grca_ctx::OUT_RING], 0);
+    };
     // A dynamic tail after a static head: its host-to-device copy runs on the
     // copy stream while the elevation cull works through the static triangles.
     const bool overlap = n_dyn && first_dyn > 0 && (uint64_t)first_dyn + n_dyn == ctx->n_tris &&
@@ -937,6 +965,7 @@ grca_status grca_cast_host(grca_ctx* ctx, const int32_t* ids, uint32_t n, const 
     }
     if (total > ctx->out_cap) {
         CK(cudaStreamSynchronize(st));
+        CK(cudaStreamSynchronize(ctx->d2h_stream));
         cudaFree(ctx->d_out_dist);
         cudaFree(ctx->d_out_tri);
         ctx->d_out_dist = nullptr;
@@ -986,7 +1015,10 @@ grca_status grca_cast_host(grca_ctx* ctx, const int32_t* ids, uint32_t n, const 
             ctx->gb_lo = ctx->gb_hi = 0;
             ctx->pending_launches++;   // the group-bound kernel enqueued between the parts
             rs = run_frame(ctx, a, cfg_for(ctx, a), st, (flags & GRCA_CAST_GRAPH) != 0, first_dyn, ctx->ev_copied,
-                           [&]() { launch_group_bounds(ctx->d_tris, ctx->n_tris, lo, hi - lo, ctx->d_gb, ctx->n_sm, st); });
+                           [&]() {
+                               wait_prev_out();
+                               launch_group_bounds(ctx->d_tris, ctx->n_tris, lo, hi - lo, ctx->d_gb, ctx->n_sm, st);
+                           });
         } else if (a.gbounds || a.bvh_nodes) {
             // group boxes (and the hierarchy split) need the new vertices first
             CK(cudaStreamWaitEvent(st, ctx->ev_copied, 0));
@@ -997,20 +1029,52 @@ grca_status grca_cast_host(grca_ctx* ctx, const int32_t* ids, uint32_t n, const 
                 ctx->pending_launches++;
                 ctx->gb_lo = ctx->gb_hi = 0;
             }
+            wait_prev_out();
             rs = run_frame(ctx, a, cfg_for(ctx, a), st, (flags & GRCA_CAST_GRAPH) != 0);
         } else {
-            rs = run_frame(ctx, a, cfg_for(ctx, a), st, (flags & GRCA_CAST_GRAPH) != 0, first_dyn, ctx->ev_copied);
+            rs = run_frame(ctx, a, cfg_for(ctx, a), st, (flags & GRCA_CAST_GRAPH) != 0, first_dyn, ctx->ev_copied,
+                           wait_prev_out);
         }
     } else {
+        wait_prev_out();
         rs = grca_cast(ctx, ids, n, ctx->d_out_dist, ctx->d_out_tri, flags, stream);
     }
     if (rs != GRCA_OK) {
         if (overlap) cudaStreamSynchronize(ctx->copy_stream);   // the host source stays in use until then
         return rs;
     }
+    if (async_out) {
+        // results go out on d2h_stream while the caller enqueues the next frame;
+        // at most OUT_RING casts have copies in flight
+        if (ctx->out_count == grca_ctx::OUT_RING) {
+            CK(cudaEventSynchronize(ctx->ev_out[ctx->out_head]));
+            ctx->out_head = (ctx->out_head + 1) % grca_ctx::OUT_RING;
+            ctx->out_count--;
+        }
+        CK(cudaEventRecord(ctx->ev_decoded, st));
+        CK(cudaStreamWaitEvent(ctx->d2h_stream, ctx->ev_decoded, 0));
+        CK(cudaMemcpyAsync(out_dist_h, ctx->d_out_dist, sizeof(float) * total, cudaMemcpyDeviceToHost, ctx->d2h_stream));
+        CK(cudaMemcpyAsync(out_tri_h, ctx->d_out_tri, sizeof(uint32_t) * total, cudaMemcpyDeviceToHost,
+                           ctx->d2h_stream));
+        CK(cudaEventRecord(ctx->ev_out[(ctx->out_head + ctx->out_count) % grca_ctx::OUT_RING], ctx->d2h_stream));
+        ctx->out_count++;
+        return GRCA_OK;
+    }
     CK(cudaMemcpyAsync(out_dist_h, ctx->d_out_dist, sizeof(float) * total, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(out_tri_h, ctx->d_out_tri, sizeof(uint32_t) * total, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    return GRCA_OK;
+}
+
+grca_status grca_host_wait(grca_ctx* ctx, uint32_t max_pending) {
+    if (!ctx) return GRCA_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    while (ctx->out_count > max_pending) {
+        const cudaError_t e = cudaEventSynchronize(ctx->ev_out[ctx->out_head]);
+        ctx->out_head = (ctx->out_head + 1) % grca_ctx::OUT_RING;
+        ctx->out_count--;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventSynchronize(copy-out)");
+    }
     return GRCA_OK;
 }
 

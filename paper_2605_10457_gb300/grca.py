@@ -25,6 +25,7 @@ CAST_DUMP_CANDIDATES = 1 << 4
 CAST_LOSSY_AREA = 1 << 5
 CAST_NO_GROUP_CULL = 1 << 6
 CAST_NO_STATIC_BVH = 1 << 7
+CAST_HOST_ASYNC = 1 << 8
 NO_HIT = 0xFFFFFFFF
 
 
@@ -67,7 +68,7 @@ EXPORTS = ["grca_create", "grca_destroy", "grca_create_sensor", "grca_set_sensor
            "grca_get_stats", "grca_last_launch_count", "grca_profile_enable", "grca_profile_read",
            "grca_status_string", "grca_last_cuda_error", "grca_cast_noalloc",
            "grca_set_ray_mask", "grca_set_sensor_azimuths", "grca_set_range_noise", "grca_build_static",
-           "grca_get_launch_config"]
+           "grca_get_launch_config", "grca_host_wait"]
 
 
 def library_path() -> str:
@@ -101,6 +102,8 @@ def _lib_handle(build_if_missing: bool = True):
     lib.grca_cast.restype = i32
     lib.grca_cast_host.argtypes = [P, P, u32, P, u32, u32, P, P, u32, P]
     lib.grca_cast_host.restype = i32
+    lib.grca_host_wait.argtypes = [P, u32]
+    lib.grca_host_wait.restype = i32
     lib.grca_autotune.argtypes = [P, P, u32, P, P, u32, P, ctypes.POINTER(ctypes.c_float)]
     lib.grca_autotune.restype = i32
     lib.grca_set_debug_dump.argtypes = [P, P, ctypes.c_uint64, P]
@@ -342,6 +345,11 @@ class Caster:
         st = self.lib.grca_cast_host(self.ctx, ids_a.ctypes.data, ids_a.shape[0], dyn_ptr, first_dyn, n_dyn,
                                      dist_ptr, tri_ptr, int(flags), stream_ptr)
         self._check(st, "grca_cast_host")
+
+    def host_wait(self, max_pending: int = 0):
+        """Block until at most `max_pending` asynchronous host casts
+        (CAST_HOST_ASYNC) still have results on their way to the host."""
+        self._check(self.lib.grca_host_wait(self.ctx, int(max_pending)), "grca_host_wait")
 
     def autotune(self, ids, flags: int = 0, out=None, stream=None) -> float:
         ids_a = np.ascontiguousarray(ids, dtype=np.int32)

@@ -64,6 +64,9 @@ def test_null_arguments_rejected_without_a_device(lib):
     for name, argtypes, args in (
             ("grca_get_launch_config", [P, P, ctypes.c_uint32, ctypes.c_uint32, P], (None, None, 1, 0, None)),
             ("grca_build_static", [P, ctypes.c_uint32, P], (None, 0, None)),
+            ("grca_host_wait", [P, ctypes.c_uint32], (None, 0)),
+            ("grca_cast_host", [P, P, ctypes.c_uint32, P, ctypes.c_uint32, ctypes.c_uint32, P, P, ctypes.c_uint32, P],
+             (None, None, 1, None, 0, 0, None, None, 0, None)),
             ("grca_set_ray_mask", [P, ctypes.c_int32, P, ctypes.c_int, P], (None, 0, None, 0, None)),
             ("grca_set_sensor_azimuths", [P, ctypes.c_int32, P], (None, 0, None)),
             ("grca_set_range_noise", [P, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64], (None, 0, 0.1, 1)),

@@ -419,3 +419,37 @@ def test_host_cast_matches_device_cast(mode):
         assert np.array_equal(out_t, t) and np.array_equal(out_d, d), (mode, frame, np.count_nonzero(out_t != t))
     g = _check(sc, tris, out_d, out_t, stratified_rays(sc.sensors, 200, seed=6))
     assert g["errors"] == 0, g
+
+
+@pytest.mark.parametrize("mode", ["plain", "range"])
+def test_async_host_casts_match_sync(mode):
+    """GRCA_CAST_HOST_ASYNC: frames enqueued back to back, each copying its
+    results out on the context's own stream while the next one runs, give the
+    same bits as synchronous host casts.  Eleven frames exceed the eight the
+    context keeps in flight, and grca_host_wait bounds them in between."""
+    from paper_2605_10457_gb300 import grca
+    sc = make_config("c4m")
+    if mode == "range":
+        for s in sc.sensors:
+            s.d_min, s.d_max = 0.05, 12.0
+    c_a, ids_a, _ = _setup(sc, frame=0)
+    c_s, ids_s, _ = _setup(sc, frame=0)
+    ns = sc.n_static
+    fl = grca.CAST_FP64_RECHECK | grca.CAST_GRAPH
+    n = sum(s.n_total for s in sc.sensors)
+    frames = (3, 11, 4, 9, 20, 1, 7, 15, 2, 30, 5)
+    dyn = [np.ascontiguousarray(sc.tris(f)[ns:]) for f in frames]
+    outs = [(np.empty(n, np.float32), np.empty(n, np.uint32)) for _ in frames]
+    for k in range(len(frames)):
+        c_a.cast_host(ids_a, dyn[k], ns, outs[k][0], outs[k][1], fl | grca.CAST_HOST_ASYNC)
+        if k % 3 == 2:
+            c_a.host_wait(2)
+    c_a.host_wait(0)
+    for k in range(len(frames)):
+        d = np.empty(n, np.float32)
+        t = np.empty(n, np.uint32)
+        c_s.cast_host(ids_s, dyn[k], ns, d, t, fl)
+        assert np.array_equal(outs[k][1], t) and np.array_equal(outs[k][0].view(np.uint32), d.view(np.uint32)), (mode, k)
+    with pytest.raises(grca.GrcaError):
+        c_a.cast(ids_a, fl | grca.CAST_HOST_ASYNC)   # the flag belongs to host casts only
+
