@@ -1428,13 +1428,19 @@ __device__ __forceinline__ void cull_b_test_pairs(const CastArgs& a, const CullS
             const uint32_t sn = meta >> 26;
             uint32_t idx = cc - o_excl + 1;   // candidate 0 was tested by the owner lane
             // quotient from the rounded-up reciprocal, then one correction
-            // step in each direction (idx < 2^24, so (float)idx is exact)
+            // step in each direction (enough for idx < 2^24, where (float)idx
+            // is exact); a quotient still off (larger spans of the no-cull
+            // debug mode, up to 1024 x 32768 candidates) takes the exact division
             uint32_t jo = (uint32_t)((float)idx * inv);
             if (jo * nr > idx) --jo;
             uint32_t io = idx - jo * nr;
             if (io >= nr) {
                 ++jo;
                 io -= nr;
+            }
+            if (io >= nr) {
+                jo = idx / nr;
+                io = idx - jo * nr;
             }
             const SensorDev& S = M.sens[sn];
             const uint32_t j = (meta & 1023u) + jo;

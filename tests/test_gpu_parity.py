@@ -303,6 +303,25 @@ def test_edge_cases():
     assert g["errors"] == 0, g
 
 
+def test_brute_mode_on_the_largest_grid():
+    """The no-cull debug mode tests every pair inline, so one pair's span is
+    the whole grid: 1024 x 32768 = 2^25 candidates, beyond the range where
+    the expansion's float quotient is exact by itself.  Brute force and the
+    culled path agree bit for bit."""
+    from paper_2605_10457_gb300.grca import CAST_BRUTE
+    s = make_sensor((0.0, 0.0, 0.0), elev=np.linspace(-1.2, 1.2, 1024), n_rays=32768)
+    tris = np.array([[[4, -1, -1], [4, 1, -1], [4, 0, 1.5]],
+                     [[-3, 2, -2], [-3, -2, -2], [-3, 0, 2]],
+                     [[0.5, 5, -0.4], [-0.5, 5, -0.4], [0, 5, 0.6]]], np.float32)
+    c = _caster()
+    sid = c.add_sensor(s)
+    c.upload(tris)
+    d0, t0 = _cast(c, [sid], 0)
+    d1, t1 = _cast(c, [sid], CAST_BRUTE)
+    assert np.count_nonzero(t0 != 0xFFFFFFFF) > 1000
+    assert np.array_equal(t0, t1) and np.array_equal(d0.view(np.uint32), d1.view(np.uint32))
+
+
 def test_sixty_four_sensors_in_one_cast():
     """The largest batch one cast takes (64 sensors), of mixed grids, poses,
     fields of view and ranges, every ray against the oracle."""
