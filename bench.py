@@ -383,7 +383,7 @@ def main():
                          h_tri[k % 2].data_ptr(), fl_e2e, sp)
         c.host_wait(1)
 
-    for k in range(2):
+    for k in range(max(3, args.warmup)):
         step_e2e(k)
     c.host_wait(0)
     barrier()
