@@ -19,6 +19,9 @@
  *     raised by device work (queue capacity overflow) are reported by
  *     grca_get_stats() on that stream.
  *   - One context per host thread; a context is bound to one CUDA device.
+ *     Its casts share the context's work buffers (keys, queues, tables), so
+ *     they run in the order issued on one stream; casts on different streams
+ *     must be ordered by the caller (events or synchronisation).
  *   - World frame: any right-handed frame; sensor axes f (forward), r (right),
  *     u (up) are orthonormal in it.  Azimuth increases from f toward r
  *     ("clockwise seen from above", Sec. 3.1), elevation upward from the
