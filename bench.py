@@ -41,7 +41,6 @@ F_CULL_B = 100.0  # FP32 flops per surviving pair: emitter frame + azimuth range
 F_SETUP = 200.0   # FP32 flops per live pair: the test setup (edge normals, error bounds)
 F_TEST = 30.0     # FP32 flops per candidate ray-triangle test
 TRI_BYTES = 36.0
-ROOT = os.path.dirname(os.path.abspath(__file__))
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2605_10457_gb300", "csrc", f) for f in ("grca_kernels.cu", "grca_internal.h")]
 
 
