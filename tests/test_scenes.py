@@ -69,3 +69,17 @@ def test_seeded_and_only_the_dynamic_part_moves():
     assert np.array_equal(t0[:ns], t1[:ns])               # the static head never moves
     assert not np.array_equal(t0[ns:], t1[ns:])           # the dynamic tail does
     assert np.all(np.isfinite(t1))
+
+
+def test_stress_set_produces_near_ties():
+    """The c5 stress set is aimed along chosen rays; where nothing nearer
+    occludes it, its coplanar overlapping pairs give near-tie sets of two or
+    more triangles (FP64 oracle, tie band 1e-6 relative)."""
+    import oracle
+    c5m = make_config("c5m")
+    rays = c5m.stress_rays
+    assert rays is not None and len(rays) >= 10
+    assert np.all((rays >= 0) & (rays < sum(s.n_total for s in c5m.sensors)))
+    ref = oracle.cast(c5m.sensors, c5m.tris(0), rays, ties=True)
+    assert np.all(np.isfinite(ref["t"]) & (ref["t"] > 0))          # every aimed ray hits something
+    assert np.count_nonzero(ref["n_ties"] >= 2) >= 3
