@@ -255,6 +255,9 @@ def main():
     ap.add_argument("--lean", action="store_true", help="headline leg only (no plain / profile / e2e legs)")
     ap.add_argument("--no-group-cull", action="store_true", help="A/B: turn off the group-level (GACP-T_g) cull")
     ap.add_argument("--no-hybrid-leg", action="store_true", help="skip the hybrid leg reported beside the headline")
+    ap.add_argument("--no-lossy-leg", action="store_true", help="skip the lossy apparent-area leg")
+    ap.add_argument("--area-eps", type=float, default=1e-6,
+                    help="eps_A of the lossy apparent-area leg (the paper's value: 1e-6)")
     ap.add_argument("--hybrid", action="store_true",
                     help="hybrid static/dynamic pipeline: static triangles through a hierarchy built once")
     ap.add_argument("--d-max", type=float, default=None,
@@ -425,6 +428,45 @@ def main():
                   "launch_config": c.launch_config(ids, FL)}
         c.build_static(0)
 
+    # --- lossy apparent-area cull (App. A.4.1 Step 1, Eq. apparent_area) at the
+    # paper's eps_A: its frame rate, and the paper's Hit% (a hit within 1 mm of
+    # the exact distance, or both miss) on every ray of one frame against the
+    # exact cast, which the parity tests hold to the FP64 oracle --------------
+    lossy = None
+    if not args.no_lossy_leg and build_s is None:
+        cl = grca.Caster(local, area_eps=args.area_eps, **caps)
+        ids_l = [cl.add_sensor(s) for s in sc.sensors]
+        cl.upload(full0)
+        out_l = cl.outputs(ids_l)
+        fl_l = FL | grca.CAST_LOSSY_AREA
+        if not args.no_autotune:
+            cl.autotune(ids_l, fl_l, out_l)
+
+        def step_lossy(k):
+            f = frame_of(rank, ws, k, args.frames)
+            cl.update(frames_dev[f], ns)
+            cl.cast(ids_l, fl_l | grca.CAST_GRAPH, out_l)
+
+        ms_l = timed(step_lossy, args.steps, args.warmup)
+        st_l = cl.stats(check=False)
+        f0 = frame_of(rank, ws, 0, args.frames)
+        cl.update(frames_dev[f0], ns)
+        cl.cast(ids_l, fl_l, out_l)
+        c.update(frames_dev[f0], ns)
+        c.cast(ids, FL, out)
+        torch.cuda.synchronize()
+        de, dl = out[0], out_l[0]
+        me, ml = torch.isfinite(de), torch.isfinite(dl)
+        close = me & ml & ((dl - de).abs() <= 1e-3)
+        hit_pct = 100.0 * float(((~me & ~ml) | close).float().mean())
+        lossy = {"value": whole_job_rate(ws, n_rays, args.steps, ms_l / 1e3), "unit": "Mrays/s",
+                 "ms_per_step": ms_l / args.steps, "eps_a": args.area_eps, "hit_pct": hit_pct,
+                 "hit_pct_rule": "hit within 1 mm of the exact distance, or both miss; every ray of one frame",
+                 "pairs_live": st_l["pairs_live"], "pairs_live_exact": st_prof["pairs_live"],
+                 "launch_config": cl.launch_config(ids_l, fl_l)}
+        cl.close()
+        del out_l
+
     # --- roofline of the dominant kernel ---------------------------------------
     peaks, src = _peaks()
     # the committed DRAM counters belong to one workload (c5, unlimited range)
@@ -488,6 +530,7 @@ def main():
         "plain": {"value": plain_value, "unit": "Mrays/s", "ms_per_step": ms_p / args.steps,
                   "path": "8 serial single-sensor FP32 casts per frame", "gpu_launches": plain_launches * args.steps},
         "hybrid": hybrid,
+        "lossy_area": lossy,
         "e2e": {"value": e2e_value, "unit": "Mrays/s", "h2d_bytes_per_step": int(nd * 36),
                 "d2h_bytes_per_step": int(n_rays * 8), "ms_per_step": 1e3 * e2e_s / e2e_steps,
                 "schedule": "grca_cast_host per frame from pinned host vertices into two alternating pairs of "
