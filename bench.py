@@ -256,6 +256,7 @@ def main():
     ap.add_argument("--no-group-cull", action="store_true", help="A/B: turn off the group-level (GACP-T_g) cull")
     ap.add_argument("--no-hybrid-leg", action="store_true", help="skip the hybrid leg reported beside the headline")
     ap.add_argument("--no-lossy-leg", action="store_true", help="skip the lossy apparent-area leg")
+    ap.add_argument("--no-variants-leg", action="store_true", help="skip the sensor-variants leg")
     ap.add_argument("--area-eps", type=float, default=1e-6,
                     help="eps_A of the lossy apparent-area leg (the paper's value: 1e-6)")
     ap.add_argument("--hybrid", action="store_true",
@@ -467,6 +468,40 @@ def main():
         cl.close()
         del out_l
 
+    # --- sensor variants (App. A.1, A.3): every LiDAR with per-ray azimuth
+    # noise (up to 0.45 of the ray spacing) and perturbed channel elevations, a
+    # random ray mask with half the rays firing, and 2 cm range noise; exact
+    # (FP32 + FP64 recheck).  Correctness is in the GPU tests. ----------------
+    variants = None
+    if not args.no_variants_leg and build_s is None:
+        from scenes import noisy_sensor, ray_mask
+        cv = grca.Caster(local, **caps)
+        sens_v = [noisy_sensor(s_, 100 + k) for k, s_ in enumerate(sc.sensors)]
+        ids_v = [cv.add_sensor(s_) for s_ in sens_v]
+        for k, (sid, s_) in enumerate(zip(ids_v, sens_v)):
+            cv.set_ray_mask(sid, ray_mask(s_, 200 + k, 0.5, "random"))
+            cv.set_range_noise(sid, 0.02, 300 + k)
+        cv.upload(full0)
+        out_v = cv.outputs(ids_v)
+        if not args.no_autotune:
+            cv.autotune(ids_v, FL, out_v)
+
+        def step_variants(k):
+            f = frame_of(rank, ws, k, args.frames)
+            cv.update(frames_dev[f], ns)
+            cv.cast(ids_v, FL | grca.CAST_GRAPH, out_v)
+
+        ms_v = timed(step_variants, args.steps, args.warmup)
+        st_v = cv.stats(check=False)
+        variants = {"value": whole_job_rate(ws, n_rays, args.steps, ms_v / 1e3), "unit": "Mrays/s",
+                    "ms_per_step": ms_v / args.steps,
+                    "sensors": "per-ray azimuth noise (0.45 ray spacing), perturbed elevations (0.3 gap), "
+                               "random ray mask (half the rays fire), range noise 2 cm",
+                    "candidates": st_v["candidates"], "candidates_exact_grid": st_prof["candidates"],
+                    "launch_config": cv.launch_config(ids_v, FL)}
+        cv.close()
+        del out_v
+
     # --- roofline of the dominant kernel ---------------------------------------
     peaks, src = _peaks()
     # the committed DRAM counters belong to one workload (c5, unlimited range)
@@ -531,6 +566,7 @@ def main():
                   "path": "8 serial single-sensor FP32 casts per frame", "gpu_launches": plain_launches * args.steps},
         "hybrid": hybrid,
         "lossy_area": lossy,
+        "sensor_variants": variants,
         "e2e": {"value": e2e_value, "unit": "Mrays/s", "h2d_bytes_per_step": int(nd * 36),
                 "d2h_bytes_per_step": int(n_rays * 8), "ms_per_step": 1e3 * e2e_s / e2e_steps,
                 "schedule": "grca_cast_host per frame from pinned host vertices into two alternating pairs of "
