@@ -165,17 +165,28 @@ typedef struct {
 } grca_stats;
 
 /* Create a context on CUDA device `device`.  `opt` may be NULL.
- * *out receives the context (owned by the library; free with grca_destroy). */
+ * *out receives the context (owned by the library; free with grca_destroy).
+ * Returns GRCA_ERR_INVALID_ARG for a null `out` or bad options (a culling
+ * block size that is not a multiple of 32 in [32, 256], a chunk size above
+ * 4096, a capacity above 2^32 - 1), GRCA_ERR_CUDA if the device cannot be
+ * used and GRCA_ERR_OOM if a work buffer cannot be allocated. */
 grca_status grca_create(grca_ctx** out, int device, const grca_options* opt);
 
 /* Free every device and host buffer of the context.  NULL is a no-op. */
 void grca_destroy(grca_ctx* ctx);
 
 /* Register a sensor (Sec. 3.1).  The description and its elevation table are
- * copied.  *out_sensor_id receives a dense id (0, 1, ...). */
+ * copied.  *out_sensor_id receives a dense id (0, 1, ...).  Returns
+ * GRCA_ERR_INVALID_ARG unless: 1 <= n_channels <= 1024 and 1 <= n_rays <=
+ * 32768; f, r, u orthonormal to 1e-9 and the origin finite; elevations
+ * finite, strictly ascending and below pi/2 in magnitude; dtheta > 0 with
+ * n_rays * dtheta <= 2 pi and |theta0| <= 4 pi; 0 <= d_min <= d_max with
+ * d_min finite (d_max may be +inf). */
 grca_status grca_create_sensor(grca_ctx* ctx, const grca_sensor_desc* desc, int32_t* out_sensor_id);
 
-/* Move a sensor: new origin and orthonormal axes (FP64, world frame). */
+/* Move a sensor: new origin and orthonormal axes (FP64, world frame); the
+ * next cast uses them.  Returns GRCA_ERR_INVALID_ARG for an unknown id, a
+ * non-finite origin or axes that are not orthonormal to 1e-9. */
 grca_status grca_set_sensor_pose(grca_ctx* ctx, int32_t sensor_id, const double origin[3], const double f[3],
                                  const double r[3], const double u[3]);
 
@@ -187,7 +198,12 @@ grca_status grca_set_sensor_pose(grca_ctx* ctx, int32_t sensor_id, const double 
 grca_status grca_upload_triangles(grca_ctx* ctx, const float* xyz, uint32_t n_tris, int where, void* stream);
 
 /* Overwrite triangles [first_tri, first_tri + n_tris) with new vertices
- * (same layout), e.g. the dynamic part of the scene every frame. */
+ * (same layout), e.g. the dynamic part of the scene every frame; `where` and
+ * the lifetime of a host source as for grca_upload_triangles.  Touching a
+ * triangle of the static hierarchy (grca_build_static) makes it stale until
+ * rebuilt; group boxes of the touched groups are refreshed by the next cast
+ * that needs them.  Returns GRCA_ERR_INVALID_ARG for a range outside the
+ * uploaded set. */
 grca_status grca_update_vertices(grca_ctx* ctx, const float* xyz, uint32_t first_tri, uint32_t n_tris, int where,
                                  void* stream);
 
