@@ -398,6 +398,16 @@ def main():
     for k in range(max(3, args.warmup)):
         step_e2e(k)
     c.host_wait(0)
+    # host-to-device bandwidth of this run (outside the timed region): the
+    # end-to-end figure follows it, and it varies between runs
+    probe_dst = torch.empty_like(frames_dev[0])
+    torch.cuda.synchronize()
+    t_p = time.perf_counter()
+    for k in range(3):
+        probe_dst.copy_(pin_frames[k % len(pin_frames)], non_blocking=True)
+    torch.cuda.synchronize()
+    h2d_gbs = 3 * nd * 36 / (time.perf_counter() - t_p) / 1e9
+    del probe_dst
     barrier()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
@@ -571,7 +581,8 @@ def main():
                 "d2h_bytes_per_step": int(n_rays * 8), "ms_per_step": 1e3 * e2e_s / e2e_steps,
                 "schedule": "grca_cast_host per frame from pinned host vertices into two alternating pairs of "
                             "pinned result arrays; a frame's copy-out overlaps the next frame, at most one "
-                            "frame in flight"},
+                            "frame in flight",
+                "h2d_gbs_probe": h2d_gbs},
         "gpu_launches": launches_per_frame * args.steps,
         "roofline": roofline,
         "cpu_baseline": cpu,
