@@ -89,3 +89,20 @@ def test_struct_layouts_match_header():
 def test_build_targets_sm103a_only():
     # the build passes exactly one -gencode, for sm_103a
     assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_sensor_descriptor_marshalling():
+    """The binding's grca_sensor_desc carries a scenes.Sensor field for field
+    (FP64 origin and axes, the elevation table by pointer, the azimuth grid
+    and the range)."""
+    import math
+    import numpy as np
+    from scenes import make_sensor
+    s = make_sensor((1.5, -0.8, 1.9), yaw=0.3, channels="t128", n_rays=2048, fov_deg=180.0, d_min=0.05, d_max=50.0)
+    d, elev = grca.sensor_desc(s)
+    assert list(d.origin) == [1.5, -0.8, 1.9]
+    assert np.allclose(list(d.f), s.f) and np.allclose(list(d.r), s.r) and np.allclose(list(d.u), s.u)
+    assert d.n_channels == 128 == elev.shape[0] and d.n_rays == 2048
+    assert [d.elev_rad[j] for j in (0, 70, 127)] == [float(s.elev[0]), float(s.elev[70]), float(s.elev[127])]
+    assert d.dtheta == s.dtheta and d.theta0 == s.theta0 and d.n_rays * d.dtheta == pytest.approx(math.pi)
+    assert (d.d_min, d.d_max) == (0.05, 50.0)
