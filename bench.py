@@ -44,11 +44,18 @@ TRI_BYTES = 36.0
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2605_10457_gb300", "csrc", f) for f in ("grca_kernels.cu", "grca_internal.h")]
 
 
-def kernels_digest() -> str:
+def kernels_digest(sources=None) -> str:
+    """SHA-256 of the kernel sources' code, with comments and whitespace
+    removed: a change of the code invalidates a committed capture, a change
+    of its comments does not."""
     import hashlib
+    import re
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        h.update(open(f, "rb").read())
+    for f in sources or KERNEL_SOURCES:
+        src = open(f).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()
 
 

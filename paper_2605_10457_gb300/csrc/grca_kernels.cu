@@ -12,7 +12,7 @@
 //              sensor per warp flush.
 //   k_cull_b   every survivor, warp-cooperative: azimuth span from the vertex
 //              projections (Sec. 3.7), then the pair setup and inline tests of
-//              small spans, or an append to the deferred queue (App. A.6, BAT
+//              small spans, or an append to the deferred queue (App. A.4.1 Step 4 and A.5.3, BAT
 //              list with ballot/popc allocation).
 //   k_expand   deferred pairs: per-channel cone/plane crossings give exact
 //              per-channel azimuth spans (Sec. 3.5, App. A.4.2 Step 1);

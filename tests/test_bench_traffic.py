@@ -38,3 +38,13 @@ def test_committed_capture_is_well_formed():
     for k in ("k_cull_a", "k_cull_b"):
         e = d["kernels"][k]
         assert e["dram_bytes_per_launch"] == e["dram_bytes_read"] + e["dram_bytes_write"] > 0
+
+
+def test_digest_follows_code_not_comments(tmp_path):
+    a = tmp_path / "k.cu"
+    a.write_text("// kernel\n__global__ void k(float* x) { x[0] = 1.f; /* one */ }\n")
+    d0 = bench.kernels_digest([str(a)])
+    a.write_text("// the kernel, described differently\n__global__ void k(float* x) {\n  x[0] = 1.f;  // one\n}\n")
+    assert bench.kernels_digest([str(a)]) == d0
+    a.write_text("__global__ void k(float* x) { x[0] = 2.f; }\n")
+    assert bench.kernels_digest([str(a)]) != d0
