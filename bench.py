@@ -40,6 +40,7 @@ F_CULL_A = 100.0  # FP32 flops per (triangle, sensor) pair: transform + elevatio
 F_CULL_B = 100.0  # FP32 flops per surviving pair: emitter frame + azimuth range + ray interval
 F_SETUP = 200.0   # FP32 flops per live pair: the test setup (edge normals, error bounds)
 F_TEST = 30.0     # FP32 flops per candidate ray-triangle test
+F_CULL = 200.0    # whole-frame unit: FP32 flops per (triangle, sensor) pair of the culls (150-250)
 TRI_BYTES = 36.0
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2605_10457_gb300", "csrc", f) for f in ("grca_kernels.cu", "grca_internal.h")]
 
@@ -82,9 +83,60 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def fp32_peak_tflops(sm_mhz: float, n_sm: int = 152) -> float:
+def fp32_peak_tflops(sm_mhz: float, n_sm: int) -> float:
     # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
     return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def frame_roofline(n_tris: int, n_rays: int, pairs: int, candidates: int, frame_ms: float, fp32_tflops: float,
+                   hbm_gbs: float) -> dict:
+    """Whole-frame roofline in the method's own units: bytes = tau * 36 (the
+    vertex stream) + rays * 24 (key init, key read, output); FP32 flops =
+    pairs * F_CULL + candidates * F_TEST; T_roof = the larger of the two
+    times at peak; frac = T_roof / measured frame time."""
+    b = n_tris * TRI_BYTES + n_rays * 24.0
+    f = pairs * F_CULL + candidates * F_TEST
+    t_mem = b / (hbm_gbs * 1e9)
+    t_alu = f / (fp32_tflops * 1e12)
+    t_roof = max(t_mem, t_alu)
+    s = frame_ms / 1e3
+    return {"bytes": b, "flops": f, "f_cull_per_pair": F_CULL, "f_test_per_candidate": F_TEST,
+            "achieved_gbs": b / s / 1e9, "achieved_tflops": f / s / 1e12,
+            "t_roof_ms": 1e3 * t_roof, "frame_ms": frame_ms, "binding": "alu" if t_alu >= t_mem else "hbm",
+            "frac": t_roof / s}
+
+
+def accuracy_rays(sc, n_per_sensor: int = 48, n_stress: int = 96, seed: int = 11) -> np.ndarray:
+    """The benchmark's graded ray sample: stratified rays of every sensor
+    (every channel when the budget allows, evenly strided azimuths) plus a
+    seeded subset of the stress-aimed rays."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from grading import stratified_rays
+    rays = stratified_rays(sc.sensors, n_per_sensor, seed=seed)
+    stress = getattr(sc, "stress_rays", None)
+    if stress is not None and len(stress) and n_stress:
+        rng = np.random.default_rng(seed)
+        rays = np.unique(np.concatenate([rays, rng.choice(stress, size=min(n_stress, len(stress)), replace=False)]))
+    return rays.astype(np.int64)
+
+
+def grade_accuracy(sc, tris, rays, results: dict, threads: int) -> tuple:
+    """Oracle pass over `rays` (timed: the cpu_baseline figure) and the error
+    statement of each GPU result against it.  results: name -> (t, id) over
+    `rays`.  Returns (per-result summaries, oracle seconds, tie-pass rays)."""
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from grading import grade, oracle_two_pass, summary
+    orc = oracle.Oracle(sc.sensors)
+    t0 = time.perf_counter()
+    ref0 = oracle.cast(orc, tris, rays, n_threads=threads)
+    t_plain = time.perf_counter() - t0
+    ref = oracle_two_pass(orc, tris, rays, list(results.values()), n_threads=threads, plain_ref=ref0)
+    out = {}
+    for name, (gt, gid) in results.items():
+        g = grade(orc, tris, ref, gt, gid)
+        out[name] = summary(g, ref, gt, gid)
+    return out, t_plain, ref["tie_pass_rays"]
 
 
 class Clocks:
@@ -252,7 +304,10 @@ def main():
     ap.add_argument("--config", default="c5")
     ap.add_argument("--frames", type=int, default=8, help="distinct animated frames kept on the device")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--cpu-budget", type=float, default=12.0,
+                    help="seconds of single-core oracle work for the single-core rate; 0 skips the oracle legs")
+    ap.add_argument("--acc-rays", type=int, default=48, help="graded stratified rays per sensor (accuracy leg)")
+    ap.add_argument("--acc-stress", type=int, default=96, help="graded stress-aimed rays (accuracy leg)")
     ap.add_argument("--ref-rays", type=int, default=None,
                     help="rays per step of the reference arm (default: 48, fewer for long runs)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="default: steps")
@@ -527,7 +582,8 @@ def main():
     dom_name, dom_v = dom
     avg_ms = dom_v["total_ms"] / max(1, dom_v["launches"])
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = fp32_peak_tflops(sm_max)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = fp32_peak_tflops(sm_max, n_sm)
     pairs = st_prof["pairs"]
     if dom_name == "k_cull_a":
         flops = pairs * F_CULL_A
@@ -543,26 +599,57 @@ def main():
     hbm_achieved = (sc.n_tris * TRI_BYTES) / (ka["total_ms"] / max(1, ka["launches"]) / 1e3) / 1e9
     roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak if fp32_peak else None, "traffic": measured_traffic(dom_name, traffic_key),
-                "peak_source": f"FP32 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (unit counts and max clock)",
+                "peak_source": f"FP32 {n_sm} SM x 128 lanes x 2 x {sm_max:.0f} MHz (unit counts and max clock)",
                 "algorithmic": {"k_cull_a": f"{F_CULL_A:.0f} flop per (tri, sensor) pair",
                                 "k_cull_b": f"{F_CULL_B:.0f} flop per surviving pair + {F_SETUP:.0f} per live pair "
                                             f"(setup) + {F_TEST:.0f} per inline test",
                                 "k_test": f"{F_TEST:.0f} flop per queued test"},
                 "avg_launch_ms": avg_ms,
                 "hbm_vertex_stream_gbs": hbm_achieved, "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                "hbm_peak_source": src}
+                "hbm_peak_source": src,
+                "frame": frame_roofline(sc.n_tris, n_rays, st_prof["pairs"], st_prof["candidates"],
+                                        ms_b / args.steps, fp32_peak, float(peaks.get("hbm_gbs", 6800.0)))}
 
+    # --- accuracy against the FP64 oracle, and the oracle's own rate -----------
+    # Frame 0 is cast again through the same caster (launch configuration of
+    # the timed frames) with FP32 + FP64 recheck and with the FP32 test only;
+    # both are graded on one ray sample with the stated tolerances (id up to
+    # near ties / shared edges, distance 1e-5 relative, hit/miss up to 1e-12
+    # rad of a silhouette) and no extra exemption for the FP32-only result.
+    # The oracle pass over that sample, on all host cores, is the cpu_baseline.
     cpu = None
+    accuracy = None
     if rank == 0 and ws == 1 and args.cpu_budget > 0:
-        n_cpu, t_cpu, cores = cpu_oracle_rate(sc, full0, args.cpu_budget)
+        rays_acc = accuracy_rays(sc, args.acc_rays, args.acc_stress)
+        f0 = frame_of(rank, ws, 0, args.frames)
+        c.update(frames_dev[f0], ns)
+        idx = torch.from_numpy(rays_acc).to(dev)
+        res = {}
+        st_acc = {}
+        for name, fl in (("fp32_recheck", FL), ("fp32_only", FL & ~grca.CAST_FP64_RECHECK)):
+            c.cast(ids, fl, out)
+            torch.cuda.synchronize()
+            st_acc[name] = c.stats(check=False)
+            res[name] = (out[0][idx].cpu().numpy(), out[1][idx].cpu().numpy().view(np.uint32))
+        cores = os.cpu_count() or 1
+        summ, t_cpu, n_tie = grade_accuracy(sc, full0, rays_acc, res, cores)
         n1, t1, _ = cpu_oracle_rate(sc, full0, min(2.0, args.cpu_budget / 4), seed=7, threads=1)
-        rate = n_cpu / t_cpu
+        rate = len(rays_acc) / t_cpu
+        n_stress = int(np.isin(rays_acc, getattr(sc, "stress_rays", np.zeros(0, np.int64))).sum())
         cpu = {"value": rate / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
-               "sample": f"{n_cpu} stratified rays of frame 0 x all {sc.n_tris} triangles, FP64 brute force, "
+               "sample": f"the accuracy sample: {len(rays_acc)} rays of frame 0 ({len(rays_acc) - n_stress} "
+                         f"stratified, {n_stress} stress-aimed) x all {sc.n_tris} triangles, FP64 brute force, "
                          f"{t_cpu:.1f} s",
                "single_core_mrays_per_s": n1 / t1 / 1e6,
                "extrapolated_frame_s": n_rays / rate,
                "extrapolation": "rays per frame / measured rate (every ray against every triangle)"}
+        accuracy = {"frame": f0, "rays": int(len(rays_acc)), "stress_rays": n_stress,
+                    "rule": "id equal, or in the oracle's near-tie set (1e-6 rel), or within 1e-7 rad of the "
+                            "GPU triangle with its plane distance within 1e-6 rel; distance within 1e-5 rel; "
+                            "hit/miss equal except within 1e-12 rad of the triangle's boundary; the same rule "
+                            "for both paths",
+                    "fp32_recheck": summ["fp32_recheck"], "fp32_only": summ["fp32_only"],
+                    "flagged_rays": st_acc["fp32_recheck"]["flagged_rays"], "tie_pass_rays": n_tie}
 
     kernel_ms = {k: v["total_ms"] / max(1, v["launches"]) for k, v in prof.items() if v["launches"]}
     line = {
@@ -593,12 +680,15 @@ def main():
         "gpu_launches": launches_per_frame * args.steps,
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "accuracy": accuracy,
         "clocks": clocks,
         "kernel_ms": kernel_ms,
         "stats": {k: st_prof[k] for k in ("pairs", "survivors", "pairs_live", "candidates", "candidates_inline",
                                           "big_pairs",
                                           "chunks", "tests", "hits", "uncertain", "ties", "flagged_rays",
-                                          "recheck_pairs", "group_culled", "bvh_node_visits", "bvh_tests")},
+                                          "recheck_pairs", "group_culled", "bvh_node_visits", "bvh_tests",
+                                          "queued_edge", "queued_t", "queued_range", "queued_orient", "queued_tie",
+                                          "kept_edge", "kept_t", "kept_range", "kept_orient", "kept_tie")},
         "autotune_ms": tune_ms,
         "launch_config": launch_cfg,
         "static_build_s": build_s,

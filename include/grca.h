@@ -162,6 +162,23 @@ typedef struct {
     uint64_t n_rays;          /* rays in the last cast */
     uint32_t device_error;    /* bit mask of device-side errors (0 = none) */
     uint32_t reserved;
+    /* FP64 re-test queue by cause, FP32+recheck casts only.  queued_*: (ray,
+     * triangle) entries the FP32 pass queued; kept_*: of those, the entries
+     * the filter kept because they may still beat or tie the ray's final FP32
+     * winner (their rays are the flagged rays).  Causes: edge = the ray passes
+     * within the FP32 error bound of an edge of the triangle; t = inside with
+     * margin but the error bound of the FP32 distance is above the accepted
+     * relative bound; range = the distance lies within its error bound of
+     * d_min or d_max; orient = the sign of (v0-o).n is within its error bound;
+     * tie = two certain FP32 hits on one ray within the tie band (both
+     * triangles queued). */
+    uint64_t queued_edge, queued_t, queued_range, queued_orient, queued_tie;
+    uint64_t kept_edge, kept_t, kept_range, kept_orient, kept_tie;
+    /* queued entries of cause t whose distance was re-evaluated in
+     * double-float FP32 arithmetic (bounded to the accepted relative error)
+     * before the filter; the settled ones are committed as certain hits or
+     * dropped as misses and are never kept. */
+    uint64_t t_refined;
 } grca_stats;
 
 /* Create a context on CUDA device `device`.  `opt` may be NULL.
@@ -313,8 +330,10 @@ grca_status grca_set_range_noise(grca_ctx* ctx, int32_t sensor_id, double sigma,
  * Its scratch memory (per-ray closest-hit keys, ray tables, counters) is one
  * fixed device array of about 2.4 MB inside the library, present on every
  * GPU that loads the library until the process exits.
- *   sensor   : as for grca_create_sensor (read during the call only).
- *   tris     : DEVICE pointer, n_tris FP32 triangles [n][3][3], 16-byte aligned.
+ *   sensor   : checked as by grca_create_sensor (read during the call only).
+ *   tris     : DEVICE pointer, n_tris FP32 triangles [n][3][3], 16-byte
+ *              aligned (else GRCA_ERR_INVALID_ARG); read up to its last
+ *              float only, so the buffer needs no padding.
  *   out_dist, out_tri : DEVICE arrays of n_channels*n_rays entries, same
  *              layout and miss convention as grca_cast.
  *   flags    : 0 or GRCA_CAST_CULL_BACKFACE; the plain FP32 test is used.
@@ -326,7 +345,14 @@ grca_status grca_set_range_noise(grca_ctx* ctx, int32_t sensor_id, double sigma,
  * call before any stream capture.  Every call on a device shares the one
  * array (each call resets what must start empty): calls that overlap on the
  * GPU (different streams, or different host threads) race and corrupt each
- * other's results. */
+ * other's results.
+ * Errors: the return value reports argument errors and this call's kernel
+ * launch errors (an error left by an earlier launch is cleared first).  No
+ * device-side error can arise: every candidate span is tested inline, so the
+ * call has no work queue that could overflow.  Spans are not split across
+ * threads here, so a triangle that covers many rays (ground under the sensor)
+ * is tested by one thread and lengthens the call; grca_cast balances such
+ * pairs over many threads. */
 grca_status grca_cast_noalloc(const grca_sensor_desc* sensor, const float* tris, uint32_t n_tris, float* out_dist,
                               uint32_t* out_tri, uint32_t flags, void* stream);
 
@@ -351,8 +377,9 @@ uint32_t grca_last_launch_count(grca_ctx* ctx);
 grca_status grca_profile_enable(grca_ctx* ctx, int enable);
 
 /* Totals since grca_profile_enable: for kernel k < min(max, *n_out) of the
- * frame sequence (k_init, k_cull_a, k_cull_b, k_expand, k_test,
- * k_recheck_filter, k_recheck_rays, k_recheck_pairs, k_decode), its name (static string), number of launches and
+ * frame sequence (k_init, k_cull_a, k_cull_b, k_expand, k_test, k_bvh,
+ * k_refine, k_recheck_filter, k_recheck_rays, k_recheck_pairs, k_decode),
+ * its name (static string), number of launches and
  * summed device time in ms.  Synchronizes with the recorded events.
  * *n_out receives the number of kernel kinds. */
 grca_status grca_profile_read(grca_ctx* ctx, uint32_t max, const char** names, uint64_t* launches,

@@ -105,6 +105,8 @@ struct grca_ctx {
     std::vector<SensorHost> sensors;
     float2* d_ch = nullptr;
     double2* d_ch64 = nullptr;
+    float2* d_ch_lo = nullptr;
+    float2* d_az_lo = nullptr;
     float2* d_az = nullptr;
     double2* d_az64 = nullptr;
     uint16_t* d_lut = nullptr;
@@ -214,7 +216,8 @@ static void free_graphs(grca_ctx* ctx) {
     ctx->graphs.clear();
 }
 
-static bool valid_axes(const double f[3], const double r[3], const double u[3]) {
+namespace grca {
+bool valid_axes(const double f[3], const double r[3], const double u[3]) {
     auto dot = [](const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
     const double* v[3] = {f, r, u};
     for (int i = 0; i < 3; ++i)
@@ -227,6 +230,27 @@ static bool valid_axes(const double f[3], const double r[3], const double u[3]) 
     }
     return true;
 }
+
+// every condition grca_create_sensor places on a description, sizes included
+bool sensor_desc_valid(const grca_sensor_desc* d) {
+    if (!d || !d->elev_rad) return false;
+    if (d->n_channels < 1 || d->n_channels > (uint32_t)MAX_CHANNELS || d->n_rays < 1 || d->n_rays > (uint32_t)MAX_RAYS)
+        return false;
+    if (!valid_axes(d->f, d->r, d->u)) return false;
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(d->origin[k])) return false;
+    for (uint32_t j = 0; j < d->n_channels; ++j) {
+        double e = d->elev_rad[j];
+        if (!std::isfinite(e) || std::fabs(e) >= M_PI / 2) return false;
+        if (j > 0 && !(e > d->elev_rad[j - 1])) return false;
+    }
+    if (!std::isfinite(d->theta0) || !std::isfinite(d->dtheta) || !(d->dtheta > 0.0)) return false;
+    if (d->n_rays * d->dtheta > 2 * M_PI + 1e-9) return false;
+    if (std::fabs(d->theta0) > 4 * M_PI) return false;
+    if (!(d->d_min >= 0.0) || !(d->d_max >= d->d_min) || !std::isfinite(d->d_min)) return false;
+    return true;
+}
+}  // namespace grca
 
 extern "C" {
 
@@ -351,6 +375,8 @@ void grca_destroy(grca_ctx* ctx) {
     cudaFree(ctx->d_bvh_tris);
     cudaFree(ctx->d_ch);
     cudaFree(ctx->d_ch64);
+    cudaFree(ctx->d_ch_lo);
+    cudaFree(ctx->d_az_lo);
     cudaFree(ctx->d_az);
     cudaFree(ctx->d_az64);
     cudaFree(ctx->d_lut);
@@ -385,21 +411,7 @@ void grca_destroy(grca_ctx* ctx) {
 }
 
 grca_status grca_create_sensor(grca_ctx* ctx, const grca_sensor_desc* d, int32_t* out_id) {
-    if (!ctx || !d || !out_id || !d->elev_rad) return GRCA_ERR_INVALID_ARG;
-    if (d->n_channels < 1 || d->n_channels > (uint32_t)MAX_CHANNELS || d->n_rays < 1 || d->n_rays > (uint32_t)MAX_RAYS)
-        return GRCA_ERR_INVALID_ARG;
-    if (!valid_axes(d->f, d->r, d->u)) return GRCA_ERR_INVALID_ARG;
-    for (int k = 0; k < 3; ++k)
-        if (!std::isfinite(d->origin[k])) return GRCA_ERR_INVALID_ARG;
-    for (uint32_t j = 0; j < d->n_channels; ++j) {
-        double e = d->elev_rad[j];
-        if (!std::isfinite(e) || std::fabs(e) >= M_PI / 2) return GRCA_ERR_INVALID_ARG;
-        if (j > 0 && !(e > d->elev_rad[j - 1])) return GRCA_ERR_INVALID_ARG;
-    }
-    if (!std::isfinite(d->theta0) || !std::isfinite(d->dtheta) || !(d->dtheta > 0.0)) return GRCA_ERR_INVALID_ARG;
-    if (d->n_rays * d->dtheta > 2 * M_PI + 1e-9) return GRCA_ERR_INVALID_ARG;
-    if (std::fabs(d->theta0) > 4 * M_PI) return GRCA_ERR_INVALID_ARG;
-    if (!(d->d_min >= 0.0) || !(d->d_max >= d->d_min) || !std::isfinite(d->d_min)) return GRCA_ERR_INVALID_ARG;
+    if (!ctx || !out_id || !sensor_desc_valid(d)) return GRCA_ERR_INVALID_ARG;
     SensorHost s;
     s.d = *d;
     s.elev.assign(d->elev_rad, d->elev_rad + d->n_channels);
@@ -591,6 +603,7 @@ static grca_status ensure_tables(grca_ctx* ctx, cudaStream_t st) {
     std::vector<double2> ch64;
     std::vector<float2> az;
     std::vector<double2> az64;
+    std::vector<float2> ch_lo, az_lo;
     std::vector<uint16_t> lut;
     ctx->ch_off.clear();
     ctx->az_off.clear();
@@ -603,6 +616,7 @@ static grca_status ensure_tables(grca_ctx* ctx, cudaStream_t st) {
             double sn = std::sin(e), cs = std::cos(e);
             ch.push_back(make_float2((float)sn, (float)cs));
             ch64.push_back(make_double2(sn, cs));
+            ch_lo.push_back(make_float2((float)(sn - (double)(float)sn), (float)(cs - (double)(float)cs)));
             sins.push_back((float)sn);
         }
         float lo, iw;
@@ -617,15 +631,20 @@ static grca_status ensure_tables(grca_ctx* ctx, cudaStream_t st) {
             double sn = std::sin(th), cs = std::cos(th);
             az.push_back(make_float2((float)sn, (float)cs));
             az64.push_back(make_double2(sn, cs));
+            az_lo.push_back(make_float2((float)(sn - (double)(float)sn), (float)(cs - (double)(float)cs)));
         }
     }
     CK(cudaStreamSynchronize(st));
     cudaFree(ctx->d_ch);
     cudaFree(ctx->d_ch64);
+    cudaFree(ctx->d_ch_lo);
+    cudaFree(ctx->d_az_lo);
     cudaFree(ctx->d_az);
     cudaFree(ctx->d_az64);
     ctx->d_ch = nullptr;
     ctx->d_ch64 = nullptr;
+    ctx->d_ch_lo = nullptr;
+    ctx->d_az_lo = nullptr;
     ctx->d_az = nullptr;
     ctx->d_az64 = nullptr;
     cudaFree(ctx->d_lut);
@@ -640,6 +659,10 @@ static grca_status ensure_tables(grca_ctx* ctx, cudaStream_t st) {
     CK(cudaMemcpy(ctx->d_ch64, ch64.data(), sizeof(double2) * ch.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_az, az.data(), sizeof(float2) * az.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_az64, az64.data(), sizeof(double2) * az.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_ch_lo, sizeof(float2) * std::max<size_t>(ch.size(), 1)));
+    CK(cudaMalloc(&ctx->d_az_lo, sizeof(float2) * std::max<size_t>(az.size(), 1)));
+    CK(cudaMemcpy(ctx->d_ch_lo, ch_lo.data(), sizeof(float2) * ch.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_az_lo, az_lo.data(), sizeof(float2) * az.size(), cudaMemcpyHostToDevice));
     ctx->tables_dirty = false;
     free_graphs(ctx);
     return GRCA_OK;
@@ -677,7 +700,10 @@ static void fill_sensor(const grca_ctx* ctx, int id, uint32_t ray_off, SensorDev
         s.o_hi[k] = hi;
         s.o_lo[k] = (float)(d.origin[k] - (double)hi);
     }
-    for (int k = 0; k < 9; ++k) s.B[k] = (float)s.B64[k];
+    for (int k = 0; k < 9; ++k) {
+        s.B[k] = (float)s.B64[k];
+        s.B_lo[k] = (float)(s.B64[k] - (double)s.B[k]);
+    }
     s.d_min64 = d.d_min;
     s.d_max64 = d.d_max;
     s.theta0 = (float)d.theta0;
@@ -770,6 +796,8 @@ static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, f
     a.ch_sc64 = ctx->d_ch64;
     a.az_sc = ctx->d_az;
     a.az_sc64 = ctx->d_az64;
+    a.ch_lo = ctx->d_ch_lo;
+    a.az_lo = ctx->d_az_lo;
     a.lut = ctx->d_lut;
     a.total_ch = (uint32_t)total_ch;
     a.n_rays_total = (uint32_t)total;
@@ -1106,6 +1134,13 @@ grca_status grca_get_stats(grca_ctx* ctx, grca_stats* out, void* stream) {
     out->bvh_tests = c[C_BVH_TESTS];
     out->n_rays = ctx->last_n_rays;
     out->device_error = err;
+    uint64_t* q = &out->queued_edge;
+    uint64_t* kp = &out->kept_edge;
+    for (int k = 0; k < UC_NUM; ++k) {
+        q[k] = c[C_QUEUED0 + k];
+        kp[k] = c[C_KEPT0 + k];
+    }
+    out->t_refined = c[C_REFINED];
     return err ? GRCA_ERR_CAPACITY : GRCA_OK;
 }
 

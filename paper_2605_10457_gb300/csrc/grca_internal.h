@@ -6,7 +6,13 @@
 
 #include <cuda_runtime.h>
 
+#include "grca.h"
+
 namespace grca {
+
+// host-side argument checks shared by the entry points (grca_api.cu)
+bool valid_axes(const double f[3], const double r[3], const double u[3]);
+bool sensor_desc_valid(const grca_sensor_desc* d);
 
 // Closest-hit key: (float bits of t) << 32 | triangle id.  For t > 0 the float
 // bits order like the floats, so a u64 min is a lexicographic (t, id) min: the
@@ -21,10 +27,23 @@ constexpr int MAX_RAYS = 32768;
 
 // queue counters (device uint32[8])
 enum { Q_BIG = 0, Q_CHUNK = 1, Q_RECHECK = 2, Q_FLAG = 3, Q_DUMP = 4, Q_SURV = 5, Q_SURV_SPLIT = 6, Q_NUM = 8 };
-// statistics counters (device u64[16])
+// statistics counters (device u64[C_NUM])
 enum {
     C_PAIRS = 0, C_PAIRS_LIVE, C_CAND, C_CAND_INLINE, C_BIG, C_CHUNKS, C_TESTS, C_HITS,
-    C_UNCERTAIN, C_TIES, C_FLAGGED, C_RECHECK, C_SURV, C_GROUP, C_BVH_VISITS, C_BVH_TESTS, C_NUM = 16
+    C_UNCERTAIN, C_TIES, C_FLAGGED, C_RECHECK, C_SURV, C_GROUP, C_BVH_VISITS, C_BVH_TESTS,
+    C_QUEUED0 = 16,   // re-test queue entries per cause (UC_*), C_QUEUED0 + cause
+    C_KEPT0 = 21,     // entries per cause kept by the filter (their rays are flagged)
+    C_REFINED = 26,   // entries of cause UC_T whose t was re-evaluated in double-float
+    C_NUM = 32
+};
+// why a (ray, triangle) pair went to the FP64 re-test queue
+enum {
+    UC_EDGE = 0,    // the ray passes within the FP32 error bound of an edge (|E_k| <= tau_k)
+    UC_T = 1,       // inside with margin, but the relative error bound of t exceeds TAU_T
+    UC_RANGE = 2,   // t within its error bound of d_min or d_max
+    UC_ORIENT = 3,  // |det| within its error bound: facing and orientation unknown
+    UC_TIE = 4,     // two certain hits on one ray within the tie band
+    UC_NUM = 5
 };
 // device error bits
 enum { ERR_BIG_CAP = 1, ERR_CHUNK_CAP = 2, ERR_RECHECK_CAP = 4, ERR_FLAG_CAP = 8, ERR_DUMP_CAP = 16, ERR_SURV_CAP = 32 };
@@ -36,6 +55,8 @@ struct SensorDev {
     double d_min64, d_max64;
     float o_hi[3], o_lo[3];  // origin = o_hi + o_lo (float pair)
     float B[9];           // rows f, r, u (FP32)
+    float B_lo[9];        // B64 - B (FP32): the double-float rotation of the t refinement
+    float pad3_;
     float theta0, dtheta, inv_dtheta;
     float d_min, d_max;
     float period;         // 2*pi/dtheta, in rays
@@ -118,6 +139,8 @@ struct CastArgs {
     const double2* ch_sc64;
     const float2* az_sc;      // (sin, cos) of ray azimuths, FP32
     const double2* az_sc64;
+    const float2* ch_lo;      // FP64 table - FP32 table (low parts): double-float directions
+    const float2* az_lo;
     const uint16_t* lut;      // channel lookup tables (LUT_BINS per registered sensor)
     uint32_t total_ch;
     uint32_t n_rays_total;
@@ -158,6 +181,8 @@ struct CastArgs {
     // survivor pass over part of the queue: 0 all; 1 the survivors queued so
     // far (and record their count); 2 the survivors queued after that
     uint32_t surv_part;
+    // elevation pass: the sensors [sens_base, sens_base + sens_count) of this launch
+    uint32_t sens_base, sens_count;
 };
 
 struct LaunchCfg {
@@ -170,7 +195,8 @@ struct LaunchCfg {
 
 // kernels of one frame, in launch order
 enum {
-    K_INIT = 0, K_CULL_A, K_CULL_B, K_EXPAND, K_TEST, K_BVH, K_RECHECK_FILTER, K_RECHECK_RAYS, K_RECHECK_PAIRS, K_DECODE,
+    K_INIT = 0, K_CULL_A, K_CULL_B, K_EXPAND, K_TEST, K_BVH, K_REFINE, K_RECHECK_FILTER, K_RECHECK_RAYS, K_RECHECK_PAIRS,
+    K_DECODE,
     K_NUM
 };
 extern const char* const kKernelNames[K_NUM];

@@ -217,7 +217,10 @@ __device__ __forceinline__ float det_error(const V3& w0, const TriW& T) {
 // ---------------------------------------------------------------------------
 // per-candidate test
 // ---------------------------------------------------------------------------
+// T_UNCERTAIN + cause: the FP32 result needs the FP64 re-test (recheck mode
+// only); the cause (UC_*) goes with the queued entry for the statistics
 enum { T_MISS = 0, T_HIT = 1, T_UNCERTAIN = 2 };
+__device__ __forceinline__ bool is_uncertain(int res) { return res >= T_UNCERTAIN; }
 
 __device__ __forceinline__ V3 ray_dir(float2 ch, float2 az) {
     // Eq. ray_dir in the emitter frame: (cos th cos ph, sin th cos ph, sin ph); (x=sin, y=cos)
@@ -276,7 +279,7 @@ __device__ __forceinline__ int test_fp32(const SV& st, const SensorDev& S, V3 d,
         // orientation unknown: the other orientation may still hold
         if (E0 <= tau0 && E1 <= tau1 && E2 <= tau2) {
             t_err = 1.f;
-            return T_UNCERTAIN;
+            return T_UNCERTAIN + UC_ORIENT;
         }
         return T_MISS;
     }
@@ -284,16 +287,18 @@ __device__ __forceinline__ int test_fp32(const SV& st, const SensorDev& S, V3 d,
     t_err = __fadd_rn(__fmaf_rn(vdot({fabsf(d.x), fabsf(d.y), fabsf(d.z)}, {st.f(18), st.f(19), st.f(20)}), fabsf(rdn),
                                 st.f(16)),
                       2.4e-7f);
+    // cause of an uncertain result, first that applies: orientation, edge, range, t
+    const int unc_base = T_UNCERTAIN + (unc_pair ? UC_ORIENT : (!inside ? UC_EDGE : UC_T));
     if (!(t > 0.f) || !(t_err < 0.25f)) {
         t_err = 1.f;
-        return (inside && !unc_pair && !(t > 0.f)) ? T_MISS : T_UNCERTAIN;
+        return (inside && !unc_pair && !(t > 0.f)) ? T_MISS : unc_base;
     }
     if (S.has_range) {
         const float lo = __fmul_rn(t, __fsub_rn(1.f, t_err)), hi = __fmul_rn(t, __fadd_rn(1.f, t_err));
         if (hi < S.d_min || lo > S.d_max) return T_MISS;
-        if (lo < S.d_min || hi > S.d_max) return T_UNCERTAIN;
+        if (lo < S.d_min || hi > S.d_max) return (inside && !unc_pair) ? T_UNCERTAIN + UC_RANGE : unc_base;
     }
-    if (!inside || unc_pair || t_err > TAU_T) return T_UNCERTAIN;
+    if (!inside || unc_pair || t_err > TAU_T) return unc_base;
     return T_HIT;
 }
 
@@ -314,10 +319,10 @@ __device__ __forceinline__ void flag_ray(const CastArgs& a, uint32_t g) {
 
 // queue (ray, triangle, lower bound of t) for the FP64 re-test; the filter
 // pass keeps it only if it can still beat or tie the ray's final FP32 winner
-__device__ __forceinline__ void push_recheck(const CastArgs& a, uint32_t g, uint32_t tri, float t_lo) {
+__device__ __forceinline__ void push_recheck(const CastArgs& a, uint32_t g, uint32_t tri, float t_lo, uint32_t cause) {
     uint32_t idx = atomicAdd(&a.qcount[Q_RECHECK], 1u);
     if (idx < a.recheck_cap)
-        a.recheck[idx] = make_uint4(g, tri, __float_as_uint(t_lo), 0u);
+        a.recheck[idx] = make_uint4(g, tri, __float_as_uint(t_lo), cause);
     else
         atomicOr(a.error, (uint32_t)ERR_RECHECK_CAP);
 }
@@ -332,6 +337,106 @@ __device__ __noinline__ void dump_candidate(const CastArgs& a, uint32_t g, uint3
     }
 }
 
+// ---------------------------------------------------------------------------
+// double-float arithmetic: a value h + l held in two FP32, explicitly rounded
+// (Knuth's two-sum, the FMA two-product and their usual combinations).
+// Error bounds below use u = 2^-24 and normalised inputs (|l| <= u |h|).
+// ---------------------------------------------------------------------------
+struct DF {
+    float h, l;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {  // exact: h + l = a + b
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {  // exact: h + l = a * b
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF df_norm(float h, float e) {
+    const float s = __fadd_rn(h, e);
+    return {s, __fsub_rn(e, __fsub_rn(s, h))};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {  // |error| <= 8 u^2 (|x| + |y|)
+    const DF s = two_sum(x.h, y.h);
+    return df_norm(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
+}
+__device__ __forceinline__ DF df_sub(DF x, DF y) { return df_add(x, DF{-y.h, -y.l}); }
+__device__ __forceinline__ DF df_mul(DF x, DF y) {  // |error| <= 8 u^2 |x| |y|
+    const DF p = two_prod(x.h, y.h);
+    return df_norm(p.h, __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, p.l)));
+}
+
+// Re-evaluation of t for a candidate whose FP32 test is certain about the hit
+// (inside every edge with margin, facing known) but whose FP32 distance has
+// an error bound above TAU_T: grazing incidence, where d.n cancels.  t =
+// ((v0 - o).n) / (D.n) in the world frame, in double-float from the FP32
+// vertices (differences exact), the origin o_hi + o_lo, the direction D =
+// B^T d from the FP64 tables as high + low parts and B as B + B_lo.  Bounds
+// from the operation bounds above: |err(n_c)| <= 16 u^2 N_c (N_c the sum of
+// the two products' magnitudes), |err(w0_c)| <= 10 u^2 (|w0_c| + |o_c|),
+// |err(det)| <= 34 u^2 M_det, |err(D_c)| <= 64 u^2, |err(D.n)| <= 88 u^2 M_dn,
+// M_det = sum_c |w0_c| (|n_c| + N_c) + |o_c| |n_c|, M_dn = sum_c |n_c| + N_c;
+// the relative bound of t adds both relative terms (taken 1.5 times) and the
+// final rounding to FP32.  Returns T_HIT (t, t_err refined), T_MISS, or
+// T_UNCERTAIN + cause (t, t_err unchanged unless the cause is the range).
+struct Refined {
+    int res;
+    float t, e;
+};
+__device__ __noinline__ Refined refine_t(const CastArgs& a, const SensorDev& S, uint32_t j, uint32_t i, uint32_t tri) {
+    const float* t9 = a.tris + 9ull * tri;
+    const float v0x = __ldg(t9 + 0), v0y = __ldg(t9 + 1), v0z = __ldg(t9 + 2);
+    const DF e1x = two_sum(__ldg(t9 + 3), -v0x), e1y = two_sum(__ldg(t9 + 4), -v0y), e1z = two_sum(__ldg(t9 + 5), -v0z);
+    const DF e2x = two_sum(__ldg(t9 + 6), -v0x), e2y = two_sum(__ldg(t9 + 7), -v0y), e2z = two_sum(__ldg(t9 + 8), -v0z);
+    const DF nx = df_sub(df_mul(e1y, e2z), df_mul(e1z, e2y));
+    const DF ny = df_sub(df_mul(e1z, e2x), df_mul(e1x, e2z));
+    const DF nz = df_sub(df_mul(e1x, e2y), df_mul(e1y, e2x));
+    const float Nx = fabsf(e1y.h * e2z.h) + fabsf(e1z.h * e2y.h), Ny = fabsf(e1z.h * e2x.h) + fabsf(e1x.h * e2z.h),
+                Nz = fabsf(e1x.h * e2y.h) + fabsf(e1y.h * e2x.h);
+    const DF wx = df_add(two_sum(v0x, -S.o_hi[0]), DF{-S.o_lo[0], 0.f});
+    const DF wy = df_add(two_sum(v0y, -S.o_hi[1]), DF{-S.o_lo[1], 0.f});
+    const DF wz = df_add(two_sum(v0z, -S.o_hi[2]), DF{-S.o_lo[2], 0.f});
+    const DF det = df_add(df_add(df_mul(wx, nx), df_mul(wy, ny)), df_mul(wz, nz));
+    // emitter-frame direction (cos th cos ph, sin th cos ph, sin ph), then D = B^T d
+    const float2 ch = __ldg(&a.ch_sc[S.ch_off + j]), chl = __ldg(&a.ch_lo[S.ch_off + j]);
+    const float2 az = __ldg(&a.az_sc[S.az_off + i]), azl = __ldg(&a.az_lo[S.az_off + i]);
+    const DF cph = {ch.y, chl.y};
+    const DF d0 = df_mul(DF{az.y, azl.y}, cph), d1 = df_mul(DF{az.x, azl.x}, cph), d2 = {ch.x, chl.x};
+    DF D[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        D[c] = df_add(df_add(df_mul(d0, DF{S.B[c], S.B_lo[c]}), df_mul(d1, DF{S.B[3 + c], S.B_lo[3 + c]})),
+                      df_mul(d2, DF{S.B[6 + c], S.B_lo[6 + c]}));
+    const DF dn = df_add(df_add(df_mul(D[0], nx), df_mul(D[1], ny)), df_mul(D[2], nz));
+    const float m_det = fabsf(wx.h) * (fabsf(nx.h) + Nx) + fabsf(wy.h) * (fabsf(ny.h) + Ny) +
+                        fabsf(wz.h) * (fabsf(nz.h) + Nz) +
+                        (fabsf(S.o_hi[0]) * fabsf(nx.h) + fabsf(S.o_hi[1]) * fabsf(ny.h) + fabsf(S.o_hi[2]) * fabsf(nz.h));
+    const float m_dn = fabsf(nx.h) + Nx + fabsf(ny.h) + Ny + fabsf(nz.h) + Nz;
+    constexpr float U2 = U32 * U32;
+    const float e = 1.02f * (51.f * U2 * m_det / fabsf(det.h) + 132.f * U2 * m_dn / fabsf(dn.h)) + 3.1e-8f;
+    Refined r{T_UNCERTAIN + UC_T, 0.f, 0.f};
+    if (!(e <= TAU_T)) return r;  // also NaN / zero det or dn
+    // t = det / dn: correctly rounded quotient of the high parts, one
+    // correction from the exact remainder
+    const float q = __fdiv_rn(det.h, dn.h);
+    const float rem = __fadd_rn(__fmaf_rn(-q, dn.h, det.h), __fmaf_rn(-q, dn.l, det.l));
+    const float t = __fadd_rn(q, __fdiv_rn(rem, dn.h));
+    if (!(t > 0.f)) {
+        r.res = T_MISS;
+        return r;
+    }
+    r.t = t;
+    r.e = e;
+    r.res = T_HIT;
+    if (S.has_range) {
+        const float lo = __fmul_rn(t, __fsub_rn(1.f, e)), hi = __fmul_rn(t, __fadd_rn(1.f, e));
+        if (hi < S.d_min || lo > S.d_max) r.res = T_MISS;
+        else if (lo < S.d_min || hi > S.d_max) r.res = T_UNCERTAIN + UC_RANGE;
+    }
+    return r;
+}
+
 // Closest-hit commit.  Certain FP32 hits go into the u64 key with
 // atomicMin (after a plain L2 load that skips hits that cannot win); in the
 // recheck mode two certain hits on one ray within the tie band queue both
@@ -343,12 +448,12 @@ __device__ __forceinline__ int commit_pre(const CastArgs& a, uint32_t g, uint32_
     if (res == T_MISS) return 0;
     unsigned long long* kp = &a.keys[g];
     float tcur = __uint_as_float((uint32_t)(cur >> 32));
-    if (res == T_UNCERTAIN) {
+    if (is_uncertain(res)) {
         // a re-test can only change the result if it may beat the current best
         const bool t_ok = t_err < 0.25f && t > 0.f;
         const float t_lo = __fmul_rn(t, __fsub_rn(1.f, t_err));
         if (t_ok && t_lo > __fmul_rn(tcur, 1.f + BETA)) return 0;
-        push_recheck(a, g, tri, t_ok ? t_lo : 0.f);
+        push_recheck(a, g, tri, t_ok ? t_lo : 0.f, (uint32_t)(res - T_UNCERTAIN));
         n_unc++;
         return 0;
     }
@@ -363,8 +468,8 @@ __device__ __forceinline__ int commit_pre(const CastArgs& a, uint32_t g, uint32_
     if (oid != NO_HIT && oid != tri) {
         float told = __uint_as_float((uint32_t)(old >> 32));
         if (fabsf(__fsub_rn(t, told)) <= __fmul_rn(BETA, fmaxf(t, told))) {
-            push_recheck(a, g, tri, __fmul_rn(t, 1.f - TAU_T));
-            push_recheck(a, g, oid, __fmul_rn(told, 1.f - TAU_T));
+            push_recheck(a, g, tri, __fmul_rn(t, 1.f - TAU_T), UC_TIE);
+            push_recheck(a, g, oid, __fmul_rn(told, 1.f - TAU_T), UC_TIE);
             n_ties++;
         }
     }
@@ -975,6 +1080,20 @@ __device__ __forceinline__ void stage_tris(const CastArgs& a, uint32_t base, uin
     __syncwarp();
 }
 
+// Same for a caller-owned buffer that ends right after triangle n_tris - 1
+// (no tail padding): whole float4s up to the buffer's end, the last 1-3
+// floats of an odd-sized tail by scalar loads.
+__device__ __forceinline__ void stage_tris_bounded(const CastArgs& a, uint32_t base, uint32_t cnt, float* dst,
+                                                   uint32_t lane) {
+    const float* src = a.tris + 9ull * base;
+    const uint32_t nf = cnt * 9u, n4 = nf >> 2;
+    __syncwarp();
+    for (uint32_t q = lane; q < n4; q += 32)
+        reinterpret_cast<float4*>(dst)[q] = __ldcs(reinterpret_cast<const float4*>(src) + q);
+    if (lane < (nf & 3u)) dst[4 * n4 + lane] = __ldcs(src + 4 * n4 + lane);
+    __syncwarp();
+}
+
 // ---------------------------------------------------------------------------
 // k_cull (fused): phase A, warp compaction of the survivors, phase B
 // ---------------------------------------------------------------------------
@@ -998,7 +1117,7 @@ __global__ void __launch_bounds__(256, 3) k_cull(CastArgs a) {
     const uint32_t gwarp = ((blockIdx.x * blockDim.x) >> 5) + wib;
     for (uint32_t base = gwarp * 32; base < a.n_tris; base += n_warps * 32) {
         const uint32_t cnt = min(32u, a.n_tris - base);
-        stage_tris(a, base, cnt, W.tri, lane);
+        stage_tris_bounded(a, base, cnt, W.tri, lane);
         bool valid = lane < cnt;
         const float* t9 = W.tri + 9 * (valid ? lane : 0);
         V3 v[3] = {{t9[0], t9[1], t9[2]}, {t9[3], t9[4], t9[5]}, {t9[6], t9[7], t9[8]}};
@@ -1063,7 +1182,7 @@ __global__ void __launch_bounds__(256, 3) k_cull(CastArgs a) {
 // per-warp shared-memory buffer (one atomic per flush of >= 256 entries)
 // record: tri | span << 32 | sensor << 53
 // ---------------------------------------------------------------------------
-constexpr int CULL_A_GROUP = 4;  // sensors per step of k_cull_a (bounds the entries a step adds)
+constexpr int ELEV_GROUP = 8;  // sensors per k_cull_a launch (the sensor loop is unrolled over them)
 constexpr int SURV_BUF = 352;    // per-warp survivor buffer; flushed before a step could overflow it
 constexpr int MAX_SENSORS_SORT = 64;
 struct CullAWarpSmem {
@@ -1073,7 +1192,7 @@ struct CullAWarpSmem {
     uint32_t hist[MAX_SENSORS_SORT];    // per-sensor counts, then bucket offsets
 };
 static_assert(sizeof(CullAWarpSmem) % 16 == 0, "per-warp staging must stay 16-byte aligned");
-static_assert(SURV_BUF >= 32 * CULL_A_GROUP, "a step must fit an empty buffer");
+static_assert(SURV_BUF >= 32 * ELEV_GROUP, "a tile must fit an empty buffer");
 
 // Flush a warp's survivor buffer to the global queue, counting-sorted by
 // sensor so that k_cull_b's batches of 32 mostly hold one sensor (uniform
@@ -1220,102 +1339,280 @@ void launch_group_bounds(const float* tris, uint32_t n_tris, uint32_t first, uin
     k_group_bounds<<<std::max(blocks, 1u), 256, 0, st>>>(tris, n_tris, g0, g1, gb);
 }
 
-// prologue of k_cull_a: sensor descriptors, channel sines and lookup tables
+// Per-sensor constants of the elevation pass, four float4 in shared memory
+// (one LDS.128 each per sensor step).  The origin's low part o_lo is not
+// subtracted per vertex: vertices are taken relative to o_hi and every bound
+// that uses them is widened by |o_lo| (olo = 1.01 |o_lo|).
+struct __align__(16) ElevSensor {
+    float ox, oy, oz, olo;       // o_hi; widening for the origin's low part
+    float ux, uy, uz, thr0;      // up axis (row u of B); pierce pre-test constant 101 olo^2 (rounded up)
+    float nlo_w, inv_w, dmax, dmin;  // LUT bin = round(s * inv_w + nlo_w); range pre-cull bounds (dmax inf: none)
+    uint32_t n_ch, sins_off, lut_off, up;   // up: 1 when the up axis is exactly (0, 0, 1)
+};
+static_assert(sizeof(ElevSensor) == 64, "four float4");
+
+// prologue of k_cull_a: the launch's sensors (full descriptors for the rare
+// paths and the group cull, packed elevation records), channel sines, lookup tables
 struct CullASmem {
     SensorDev* sens;
+    ElevSensor* es;
     float* sins;
     uint16_t* lut;
     unsigned char* rest;
 };
+// Layout: the 16-byte ElevSensor records first (read as float4), then the
+// SensorDev copies (8-byte aligned after them), the sines and the tables.
+static_assert(sizeof(ElevSensor) % 16 == 0 && sizeof(SensorDev) % alignof(SensorDev) == 0 &&
+                  alignof(SensorDev) <= 16,
+              "k_cull_a shared-memory layout");
+__device__ __forceinline__ size_t cull_a_head_bytes(uint32_t ns, uint32_t n_ch) {
+    const size_t off = sizeof(ElevSensor) * ns + sizeof(SensorDev) * ns + sizeof(float) * n_ch +
+                       sizeof(uint16_t) * LUT_BINS * ns;
+    return (off + 15) & ~size_t(15);
+}
 __device__ __forceinline__ CullASmem cull_a_prologue(const CastArgs& a, unsigned char* smem) {
     CullASmem m;
-    m.sens = reinterpret_cast<SensorDev*>(smem);
-    m.sins = reinterpret_cast<float*>(smem + sizeof(SensorDev) * a.n_sensors);
-    m.lut = reinterpret_cast<uint16_t*>(smem + sizeof(SensorDev) * a.n_sensors + sizeof(float) * a.total_ch);
-    size_t off = sizeof(SensorDev) * a.n_sensors + sizeof(float) * a.total_ch + sizeof(uint16_t) * LUT_BINS * a.n_sensors;
-    m.rest = smem + ((off + 15) & ~size_t(15));
-    for (uint32_t q = threadIdx.x; q < a.n_sensors * (uint32_t)(sizeof(SensorDev) / 4); q += blockDim.x)
-        reinterpret_cast<uint32_t*>(m.sens)[q] = reinterpret_cast<const uint32_t*>(a.sensors)[q];
+    const uint32_t ns = a.sens_count, s0 = a.sens_base;
+    m.es = reinterpret_cast<ElevSensor*>(smem);
+    m.sens = reinterpret_cast<SensorDev*>(smem + sizeof(ElevSensor) * ns);
+    m.sins = reinterpret_cast<float*>(smem + (sizeof(SensorDev) + sizeof(ElevSensor)) * ns);
+    // the sines of the launch's sensors take at most total_ch entries
+    m.lut = reinterpret_cast<uint16_t*>(smem + (sizeof(SensorDev) + sizeof(ElevSensor)) * ns + sizeof(float) * a.total_ch);
+    m.rest = smem + cull_a_head_bytes(ns, a.total_ch);
+    for (uint32_t q = threadIdx.x; q < ns * (uint32_t)(sizeof(SensorDev) / 4); q += blockDim.x)
+        reinterpret_cast<uint32_t*>(m.sens)[q] = reinterpret_cast<const uint32_t*>(a.sensors + s0)[q];
     __syncthreads();
-    for (uint32_t sn = 0; sn < a.n_sensors; ++sn) {
-        const SensorDev& S = m.sens[sn];
-        for (uint32_t j = threadIdx.x; j < S.n_ch; j += blockDim.x) m.sins[S.ch_loc + j] = a.ch_sc[S.ch_off + j].x;
-        for (uint32_t b = threadIdx.x; b < LUT_BINS; b += blockDim.x) m.lut[sn * LUT_BINS + b] = a.lut[S.lut_off + b];
+    uint32_t ch_at = 0;
+    for (uint32_t k = 0; k < ns; ++k) {
+        const SensorDev& S = m.sens[k];
+        for (uint32_t j = threadIdx.x; j < S.n_ch; j += blockDim.x) m.sins[ch_at + j] = a.ch_sc[S.ch_off + j].x;
+        for (uint32_t b = threadIdx.x; b < LUT_BINS; b += blockDim.x) m.lut[k * LUT_BINS + b] = a.lut[S.lut_off + b];
+        if (threadIdx.x == 0) {
+            ElevSensor E;
+            E.ox = S.o_hi[0];
+            E.oy = S.o_hi[1];
+            E.oz = S.o_hi[2];
+            const float olo = sqrtf(S.o_lo[0] * S.o_lo[0] + S.o_lo[1] * S.o_lo[1] + S.o_lo[2] * S.o_lo[2]);
+            E.olo = 1.01f * olo;
+            E.ux = S.B[6];
+            E.uy = S.B[7];
+            E.uz = S.B[8];
+            E.thr0 = 101.1f * E.olo * E.olo;
+            E.inv_w = S.lut_inv_w;
+            E.nlo_w = -S.lut_lo * S.lut_inv_w - 0.25f;
+            E.dmax = S.d_max < INFINITY ? S.d_max * (1.f + 2e-5f) + 2e-6f + E.olo : INFINITY;
+            E.dmin = S.d_min * (1.f - 2e-5f) - 2e-6f - E.olo;
+            E.n_ch = S.n_ch;
+            E.sins_off = ch_at;
+            E.lut_off = k * LUT_BINS;
+            E.up = S.B[6] == 0.f && S.B[7] == 0.f && S.B[8] == 1.f ? 1u : 0u;
+            m.es[k] = E;
+        }
+        ch_at += S.n_ch;
     }
     __syncthreads();
     return m;
 }
 
-template <bool RECHECK, bool BRUTE, bool GROUPS>
+// first channel whose sine is >= x: lookup-table bin, then a short forward
+// scan.  The bin is round(fb - 1/4) (nlo_w holds the -1/4), taken with one
+// addition of 1.5 * 2^23, so the bin's start lies at least a quarter bin
+// below x: within the table's half-bin slack, with room for rounding.
+__device__ __forceinline__ int chan_first(const ElevSensor& E, const float* sins, const uint16_t* lut, float x) {
+    const float fb = fminf(fmaxf(fmaf(x, E.inv_w, E.nlo_w), 0.f), (float)(LUT_BINS - 1));
+    const uint32_t bin = __float_as_uint(fb + 12582912.f) & 0x3FFFFFu;   // round(fb), 0 <= fb < 2^22
+    int j = lut[bin];
+    const int n = (int)E.n_ch;
+    while (j < n && sins[j] < x) ++j;
+    return j;
+}
+
+// Phase A of one (triangle, sensor) pair: back-face cull (if requested), the
+// range pre-cull, and the channel span from the elevation range.  Returns
+// false when culled.  Elevation range (sine space): vertex values, widened by
+// dev = 0.31 ee_max / r2min, which bounds how far any edge's great-circle arc
+// rises above (or dips below) its endpoints: an arc of angular length alpha
+// deviates by at most 1 - cos(alpha / 2) <= alpha^2 / 8 from its higher
+// endpoint, and alpha <= (pi / 2) |e| / min(|a|, |b|), so alpha^2 / 8 <=
+// (pi^2 / 32) ee / m2 < 0.3085 ee / m2 for every edge; plus |o_lo| / r_min
+// for the origin's low part and the FP32 padding EPS_S.  When the vertical
+// axis may meet the triangle, the exact test decides and the range opens to
+// the pole(s).
+// the rare paths of cull_elev, out of line to keep the hot loop small
+// back-face cull with the exact origin offset: false when culled
+__device__ __noinline__ bool elev_facing(const SensorDev& S, V3 v0, V3 v1, V3 v2, uint32_t flags) {
+    const V3 w0 = rel_origin(S, v0);
+    const V3 e1 = vsub(v1, v0), e2 = vsub(v2, v0);
+    const V3 nw = vcross(e1, e2);
+    const float det = vdot(w0, nw);
+    if (det > 0.f) {
+        if (!(flags & 1u)) return false;
+        const V3 N = {fabsf(e1.y * e2.z) + fabsf(e1.z * e2.y), fabsf(e1.z * e2.x) + fabsf(e1.x * e2.z),
+                      fabsf(e1.x * e2.y) + fabsf(e1.y * e2.x)};
+        if (det > backface_err(w0, nw, N)) return false;  // facing <=> det < 0
+    }
+    return true;
+}
+// Eq. apparent_area with the exact origin offset, A_T (c-o).n^ = (c-o).n / 2: false when culled
+__device__ __noinline__ bool elev_area_keep(const SensorDev& S, V3 v0, V3 v1, V3 v2, float area_eps2) {
+    const V3 wv[3] = {rel_origin(S, v0), rel_origin(S, v1), rel_origin(S, v2)};
+    const V3 nw = vcross(vsub(v1, v0), vsub(v2, v0));
+    V3 wc = {(wv[0].x + wv[1].x + wv[2].x) * (1.f / 3.f), (wv[0].y + wv[1].y + wv[2].y) * (1.f / 3.f),
+             (wv[0].z + wv[1].z + wv[2].z) * (1.f / 3.f)};
+    float dc = 0.5f * (wc.x * nw.x + wc.y * nw.y + wc.z * nw.z);
+    float r2c = wc.x * wc.x + wc.y * wc.y + wc.z * wc.z;
+    return !(dc * dc < area_eps2 * r2c * r2c * r2c);
+}
+// exact vertical-axis test: bit 0 pierced, bit 1 open to +1, bit 2 open to -1
+__device__ __noinline__ uint32_t elev_pierce(const SensorDev& S, V3 v0, V3 v1, V3 v2) {
+    const V3 p[3] = {rotB(S.B, rel_origin(S, v0)), rotB(S.B, rel_origin(S, v1)), rotB(S.B, rel_origin(S, v2))};
+    if (!axis_pierces(p)) return 0u;
+    return 1u | (fmaxf(p[0].z, fmaxf(p[1].z, p[2].z)) > 0.f ? 2u : 0u) |
+           (fminf(p[0].z, fminf(p[1].z, p[2].z)) < 0.f ? 4u : 0u);
+}
+
+__device__ __forceinline__ bool cull_elev(const ElevSensor& E, const SensorDev& S, const float* sins, const uint16_t* lut,
+                                          const V3 v[3], float ee_max, float lmax, uint32_t flags, float area_eps2,
+                                          uint32_t& span) {
+    if ((flags & 2u) && !elev_facing(S, v[0], v[1], v[2], flags)) return false;
+    if (flags & 4u) {  // no culling (debug)
+        span = pack_span(0, (int)S.n_ch - 1, false);
+        return true;
+    }
+    float z[3], r2[3], h2[3];
+    if (E.up) {  // warp-uniform: an upright sensor needs no projection on u
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float wx = v[k].x - E.ox, wy = v[k].y - E.oy, wz = v[k].z - E.oz;
+            z[k] = wz;
+            h2[k] = fmaf(wy, wy, wx * wx);
+            r2[k] = fmaf(wz, wz, h2[k]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float wx = v[k].x - E.ox, wy = v[k].y - E.oy, wz = v[k].z - E.oz;
+            z[k] = fmaf(E.uz, wz, fmaf(E.uy, wy, E.ux * wx));
+            r2[k] = fmaf(wz, wz, fmaf(wy, wy, wx * wx));
+            h2[k] = fmaf(-z[k], z[k], r2[k]);
+        }
+    }
+    if (E.dmax < INFINITY) {
+        // range pre-cull (App. A.4.1 Step 1), only where provably empty: every
+        // point of the triangle lies within lmax (the longest edge) of vertex 0
+        const float d0 = sqrtf(r2[0]);
+        if (d0 - lmax > E.dmax || d0 + lmax < E.dmin) return false;
+    }
+    if ((flags & 32u) && !elev_area_keep(S, v[0], v[1], v[2], area_eps2)) return false;
+    // a vertex at the origin gives 0 * inf = NaN, which fminf / fmaxf skip;
+    // r2min = 0 then makes dev huge below, so the range opens fully
+    const float sv0 = z[0] * rsqrtf(r2[0]), sv1 = z[1] * rsqrtf(r2[1]), sv2 = z[2] * rsqrtf(r2[2]);
+    const float smin = fminf(sv0, fminf(sv1, sv2)), smax = fmaxf(sv0, fmaxf(sv1, sv2));
+    const float r2min = fminf(r2[0], fminf(r2[1], r2[2]));
+    const float r2max = fmaxf(r2[0], fmaxf(r2[1], r2[2]));
+    const float h2min = fminf(h2[0], fminf(h2[1], h2[2]));
+    const float rinv = rsqrtf(fmaxf(r2min, 1e-37f));
+    // |w[k1]-w[k]|^2 <= 1.0001 |E|^2 + 5.7e-10 |w|^2 for the FP32 rounding of w
+    const float ee_p = fmaf(5.7e-10f, r2max, 1.0001f * ee_max);
+    const float dev = fmaf(0.3100004f * ee_p, rinv * rinv, fmaf(E.olo, rinv, EPS_S));
+    // (smin, smax are NaN only when every vertex sits at the origin: zero area,
+    // never tested; a non-finite vertex takes the overflow branch below)
+    float lo = smin - dev, hi = smax + dev;
+    bool pierced = false;
+    // the vertical axis can meet the projected triangle only if its nearest
+    // vertex lies within the longest edge of the axis (with margins for the
+    // FP32 rounding and for o_lo: (h + d)^2 <= 1.01 h^2 + 101 d^2)
+    if (h2min <= fmaf(8.2f * U32, r2max, fmaf(1.0201f, ee_max, E.thr0)) || !(r2max < 3e38f)) {
+        if (!(r2max < 3e38f)) {
+            // a vertex so far away that |w|^2 overflows: every channel, full circle
+            lo = -2.f;
+            hi = 2.f;
+            pierced = true;
+        } else {
+            const uint32_t pc = elev_pierce(S, v[0], v[1], v[2]);
+            pierced = pc & 1u;
+            if (pc & 2u) hi = 2.f;
+            if (pc & 4u) lo = -2.f;
+        }
+    }
+    const int n = (int)E.n_ch;
+    const int jl = chan_first(E, sins, lut, lo);
+    if (jl >= n) return false;
+    float sj = sins[jl];
+    if (sj > hi) return false;  // no channel in the range
+    int jh = jl;
+    while (jh + 1 < n) {
+        sj = sins[jh + 1];
+        if (sj > hi) break;
+        ++jh;
+    }
+    span = pack_span(jl, jh, pierced);
+    return true;
+}
+
+// k_cull_a: phase A for the sensors [sens_base, sens_base + sens_count) of
+// the cast (at most ELEV_GROUP; larger casts launch once per group).  A warp
+// stages 32 triangles, keeps their sensor-independent terms in registers and
+// runs the unrolled sensor loop over them; survivors go through the warp's
+// shared-memory buffer to the global queue.
+template <bool GROUPS>
 __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     CullASmem M = cull_a_prologue(a, smem);
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     CullAWarpSmem& W = reinterpret_cast<CullAWarpSmem*>(M.rest)[wib];
-    const bool cull_back = a.flags & 2u;
-    const bool lossy_area = a.flags & 32u;
+    const uint32_t flags = a.flags;
+    const uint32_t ns = a.sens_count, s0 = a.sens_base;
     uint32_t fill = 0;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t gwarp = ((blockIdx.x * blockDim.x) >> 5) + wib;
-    constexpr bool groups = GROUPS && !BRUTE;
+    const bool groups = GROUPS && !(flags & 4u);
     uint32_t g_culled = 0;
     // triangles [0, tri_first) belong to the static hierarchy in a hybrid cast
     const uint32_t first = a.tri_first, base0 = first & ~31u;
     for (uint32_t base = base0 + gwarp * 32; base < a.n_tris; base += n_warps * 32) {
         const uint32_t cnt = min(32u, a.n_tris - base);
         const uint32_t skip = first > base ? first - base : 0u;  // leading lanes outside the range
-        unsigned long long live = ~0ull;
+        uint32_t live = 0xFFu;
         if (groups) {
-            // GACP-T_g: lane s tests sensor s against the group's box
+            // GACP-T_g: lane k tests sensor k against the group's box
             const float4 lo = __ldg(&a.gbounds[2u * (base / GROUP_TRIS)]);
             const float4 hi = __ldg(&a.gbounds[2u * (base / GROUP_TRIS) + 1u]);
-            live = 0;
-            for (uint32_t s0 = 0; s0 < a.n_sensors; s0 += 32) {
-                const uint32_t sn = s0 + lane;
-                const bool ok = sn < a.n_sensors &&
-                                group_may_hit(M.sens[sn], M.sins + M.sens[sn].ch_loc, M.lut + sn * LUT_BINS, lo, hi);
-                live |= (unsigned long long)__ballot_sync(0xffffffffu, ok) << s0;
-            }
-            g_culled += (a.n_sensors - (uint32_t)__popcll(live)) * (cnt - skip);
+            const bool ok = lane < ns && group_may_hit(M.sens[lane], M.sins + M.es[min(lane, ns - 1)].sins_off,
+                                                       M.lut + min(lane, ns - 1) * LUT_BINS, lo, hi);
+            live = __ballot_sync(0xffffffffu, ok);
+            g_culled += (ns - (uint32_t)__popc(live)) * (cnt - skip);
             if (g_culled >= 0x40000000u && lane == 0) {
                 atomicAdd(&a.counters[C_GROUP], (unsigned long long)g_culled);
                 g_culled = 0;
             }
             if (live == 0) continue;  // the whole tile: no load, no per-triangle work
         }
+        if (fill + 32 * ns > SURV_BUF) flush_survivors(a, W, fill, lane, a.n_sensors);
         stage_tris(a, base, cnt, W.tri, lane);
         bool valid = lane < cnt && lane >= skip;
         const float* t9 = W.tri + 9 * (valid ? lane : 0);
-        V3 v[3] = {{t9[0], t9[1], t9[2]}, {t9[3], t9[4], t9[5]}, {t9[6], t9[7], t9[8]}};
-        V3 nw = vcross(vsub(v[1], v[0]), vsub(v[2], v[0]));
+        const V3 v[3] = {{t9[0], t9[1], t9[2]}, {t9[3], t9[4], t9[5]}, {t9[6], t9[7], t9[8]}};
+        const V3 e0 = vsub(v[1], v[0]), e1 = vsub(v[2], v[1]), e2 = vsub(v[0], v[2]);
+        const V3 nw = vcross(e0, vneg(e2));
         if (nw.x == 0.f && nw.y == 0.f && nw.z == 0.f) valid = false;  // zero area: never hit
-        float eeT[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            V3 e = vsub(v[k == 2 ? 0 : k + 1], v[k]);
-            eeT[k] = vdot(e, e);
+        // longest edge (squared; and rounded-up length), sensor independent
+        const float ee_max = fmaxf(vdot(e0, e0), fmaxf(vdot(e1, e1), vdot(e2, e2)));
+        const float lmax = sqrtf(ee_max) * (1.f + 1e-6f);
+#pragma unroll 1
+        for (uint32_t k = 0; k < ns; ++k) {
+            if (!((live >> k) & 1u)) continue;  // warp-uniform
+            uint32_t span = 0;
+            const bool ok = valid && cull_elev(M.es[k], M.sens[k], M.sins + M.es[k].sins_off, M.lut + k * LUT_BINS, v,
+                                                  ee_max, lmax, flags, a.area_eps2, span);
+            const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+            if (ok)
+                W.buf[fill + __popc(bal & ((1u << lane) - 1u))] = (unsigned long long)(base + lane) |
+                                                                   ((unsigned long long)span << 32) |
+                                                                   ((unsigned long long)(s0 + k) << 53);
+            fill += __popc(bal);
         }
-        // longest edge, rounded up (sensor independent)
-        const float lmax = sqrtf(fmaxf(eeT[0], fmaxf(eeT[1], eeT[2]))) * (1.f + 1e-6f);
-        for (uint32_t sg = 0; sg < a.n_sensors; sg += CULL_A_GROUP) {
-            const uint32_t ng = min((uint32_t)CULL_A_GROUP, a.n_sensors - sg);
-            if (fill + 32 * CULL_A_GROUP > SURV_BUF) flush_survivors(a, W, fill, lane, a.n_sensors);
-            for (uint32_t k = 0; k < ng; ++k) {
-                if (!((live >> (sg + k)) & 1ull)) continue;  // warp-uniform
-                uint32_t span = 0;
-                const SensorDev& S = M.sens[sg + k];
-                bool ok = valid && cull_elevation<RECHECK, BRUTE>(S, M.sins + S.ch_loc, M.lut + (sg + k) * LUT_BINS, v,
-                                                                  nw, eeT, lmax, cull_back, lossy_area, a.area_eps2,
-                                                                  span);
-                uint32_t bal = __ballot_sync(0xffffffffu, ok);
-                if (ok)
-                    W.buf[fill + __popc(bal & ((1u << lane) - 1u))] =
-                        (unsigned long long)(base + lane) | ((unsigned long long)span << 32) |
-                        ((unsigned long long)(sg + k) << 53);
-                fill += __popc(bal);
-            }
-            __syncwarp();
-        }
+        __syncwarp();
     }
     flush_survivors(a, W, fill, lane, a.n_sensors);
     if (groups && lane == 0 && g_culled) atomicAdd(&a.counters[C_GROUP], (unsigned long long)g_culled);
@@ -1791,7 +2088,7 @@ __global__ void __launch_bounds__(256) k_expand(CastArgs a) {
 // k_test: one warp per chunk of one (pair, channel) row
 // ---------------------------------------------------------------------------
 template <bool RECHECK>
-__global__ void __launch_bounds__(256) k_test(CastArgs a) {
+__global__ void __launch_bounds__(256, 4) k_test(CastArgs a) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -1894,22 +2191,82 @@ __device__ unsigned long long test_fp64(const CastArgs& a, uint32_t g, uint32_t 
     return ((unsigned long long)__float_as_uint(tf) << 32) | tri;
 }
 
+// R-1: the queued entries uncertain only in t (cause UC_T) get t re-evaluated
+// in double-float (refine_t).  A settled hit is committed like a certain FP32
+// hit (key minimum, tie detection against the returned key) and its entry
+// retired (triangle NO_HIT); a settled miss is retired; an entry still
+// uncertain stays for the FP64 re-test.  Runs after every FP32 test of the
+// frame, before the filter, so the commit order does not matter: the tie
+// chain of the FP32 commits holds for any order.
+__global__ void k_refine(CastArgs a) {
+    const uint32_t np = min(*(volatile uint32_t*)&a.qcount[Q_RECHECK], a.recheck_cap);
+    uint32_t n_ref = 0, n_hit = 0, n_ties = 0;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
+        const uint4 e = a.recheck[q];
+        if (e.w != (uint32_t)UC_T) continue;
+        uint32_t sn, j, i;
+        decode_ray(a, e.x, sn, j, i);
+        const Refined rf = refine_t(a, a.sensors[sn], j, i, e.y);
+        n_ref++;
+        if (rf.res == T_UNCERTAIN + UC_T) continue;
+        if (rf.res == T_UNCERTAIN + UC_RANGE) {
+            a.recheck[q] = make_uint4(e.x, e.y, __float_as_uint(__fmul_rn(rf.t, __fsub_rn(1.f, rf.e))), UC_RANGE);
+            continue;
+        }
+        a.recheck[q].y = NO_HIT;  // retired: settled here
+        if (rf.res != T_HIT) continue;
+        n_hit++;
+        const float t = rf.t;
+        unsigned long long* kp = &a.keys[e.x];
+        const float tcur = __uint_as_float((uint32_t)(__ldcg(kp) >> 32));
+        if (t > __fmul_rn(tcur, 1.f + BETA)) continue;
+        const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | e.y;
+        const unsigned long long old = atomicMin(kp, key);
+        const uint32_t oid = (uint32_t)old;
+        if (oid != NO_HIT && oid != e.y) {
+            const float told = __uint_as_float((uint32_t)(old >> 32));
+            if (fabsf(__fsub_rn(t, told)) <= __fmul_rn(BETA, fmaxf(t, told))) {
+                push_recheck(a, e.x, e.y, __fmul_rn(t, 1.f - TAU_T), UC_TIE);
+                push_recheck(a, e.x, oid, __fmul_rn(told, 1.f - TAU_T), UC_TIE);
+                n_ties++;
+            }
+        }
+    }
+    warp_add(&a.counters[C_REFINED], n_ref);
+    warp_add(&a.counters[C_HITS], n_hit);
+    warp_add(&a.counters[C_TIES], n_ties);
+}
+
 // R0: keep the queued pairs that can still beat or tie the ray's final FP32
 // winner (t_lo <= t_best (1 + beta)); flag their rays; drop the rest.  A kept
 // pair whose triangle is the ray's FP32 winner is flagged but not kept: R1
 // re-tests the winner of every flagged ray, so R2 would repeat that test.
+// Also counts the queued and the kept entries per cause (UC_*).
 __global__ void k_recheck_filter(CastArgs a) {
     uint32_t np = min(*(volatile uint32_t*)&a.qcount[Q_RECHECK], a.recheck_cap);
+    uint32_t nq[UC_NUM] = {}, nk[UC_NUM] = {};
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
         uint4 e = a.recheck[q];
         const unsigned long long kb = a.keys[e.x];
         float tbest = __uint_as_float((uint32_t)(kb >> 32));
-        if (__uint_as_float(e.z) <= __fmul_rn(tbest, 1.f + BETA)) {
+        // entries retired by k_refine count as queued, never as kept
+        const bool kept = e.y != NO_HIT && __uint_as_float(e.z) <= __fmul_rn(tbest, 1.f + BETA);
+#pragma unroll
+        for (int k = 0; k < UC_NUM; ++k) {
+            nq[k] += e.w == (uint32_t)k;
+            nk[k] += kept && e.w == (uint32_t)k;
+        }
+        if (kept) {
             flag_ray(a, e.x);
             if (e.y == (uint32_t)kb) a.recheck[q].y = NO_HIT;
-        } else {
+        } else if (e.y != NO_HIT) {
             a.recheck[q].y = NO_HIT;
         }
+    }
+#pragma unroll
+    for (int k = 0; k < UC_NUM; ++k) {
+        warp_add(&a.counters[C_QUEUED0 + k], nq[k]);
+        warp_add(&a.counters[C_KEPT0 + k], nk[k]);
     }
 }
 
@@ -2186,8 +2543,8 @@ size_t cull_smem_bytes(const CastArgs& a, const LaunchCfg& cfg) {
     off = (off + 15) & ~size_t(15);
     return off + sizeof(CullWarpSmem) * (size_t)(cfg.cull_block / 32);
 }
-static size_t cull_a_smem_bytes(const CastArgs& a, const LaunchCfg& cfg) {
-    size_t off = sizeof(SensorDev) * a.n_sensors + sizeof(float) * a.total_ch + sizeof(uint16_t) * LUT_BINS * a.n_sensors;
+static size_t cull_a_smem_bytes(uint32_t ns, uint32_t n_ch, const LaunchCfg& cfg) {
+    size_t off = sizeof(SensorDev) * ns + sizeof(ElevSensor) * ns + sizeof(float) * n_ch + sizeof(uint16_t) * LUT_BINS * ns;
     off = (off + 15) & ~size_t(15);
     return off + sizeof(CullAWarpSmem) * (size_t)(cfg.cull_block / 32);
 }
@@ -2202,8 +2559,8 @@ static void ensure_smem_attr(K kernel, size_t smem) {
 }
 
 const char* const kKernelNames[K_NUM] = {"k_init",  "k_cull_a",         "k_cull_b",       "k_expand",
-                                         "k_test",  "k_bvh",            "k_recheck_filter", "k_recheck_rays",
-                                         "k_recheck_pairs", "k_decode"};
+                                         "k_test",  "k_bvh",            "k_refine",         "k_recheck_filter",
+                                         "k_recheck_rays", "k_recheck_pairs", "k_decode"};
 
 // elevation cull of triangles [a.tri_first, a.n_tris) (ac) and/or the
 // survivor pass of the whole cast (a)
@@ -2211,19 +2568,26 @@ template <bool R, bool B>
 static void launch_cull_split(const CastArgs& a, const CastArgs& ac, bool do_a, bool do_b, const LaunchCfg& cfg,
                               int n_sm, cudaStream_t st, const std::function<void(int, int)>& mark) {
     if (do_a) {
-        const size_t sa = cull_a_smem_bytes(ac, cfg);
         const bool groups = !B && ac.gbounds != nullptr;
-        ensure_smem_attr(k_cull_a<R, B, false>, sa);
-        if (groups) ensure_smem_attr(k_cull_a<R, B, true>, sa);
         const uint32_t span = ac.n_tris > (ac.tri_first & ~31u) ? ac.n_tris - (ac.tri_first & ~31u) : 0u;
         const uint32_t max_blocks = (span + cfg.cull_block - 1) / cfg.cull_block;
         const int grid_a =
             (int)std::min<uint32_t>(std::max<uint32_t>(max_blocks, 1u), (uint32_t)(n_sm * cfg.cull_blocks_per_sm));
         mark(K_CULL_A, 0);
-        if (groups)
-            k_cull_a<R, B, true><<<grid_a, cfg.cull_block, sa, st>>>(ac);
-        else
-            k_cull_a<R, B, false><<<grid_a, cfg.cull_block, sa, st>>>(ac);
+        // one launch per group of ELEV_GROUP sensors
+        for (uint32_t g0 = 0; g0 < ac.n_sensors; g0 += ELEV_GROUP) {
+            CastArgs ag = ac;
+            ag.sens_base = g0;
+            ag.sens_count = std::min<uint32_t>(ELEV_GROUP, ac.n_sensors - g0);
+            const size_t sa = cull_a_smem_bytes(ag.sens_count, ag.total_ch, cfg);
+            if (groups) {
+                ensure_smem_attr(k_cull_a<true>, sa);
+                k_cull_a<true><<<grid_a, cfg.cull_block, sa, st>>>(ag);
+            } else {
+                ensure_smem_attr(k_cull_a<false>, sa);
+                k_cull_a<false><<<grid_a, cfg.cull_block, sa, st>>>(ag);
+            }
+        }
         mark(K_CULL_A, 1);
     }
     if (do_b) {
@@ -2264,7 +2628,7 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
         launch_cull_split<false, true>(ab, ac, true, true, cfg, n_sm, st, mark);
     else
         launch_cull_split<false, false>(ab, ac, true, true, cfg, n_sm, st, mark);
-    launches += 2;
+    launches += 1 + (int)((a.n_sensors + ELEV_GROUP - 1) / ELEV_GROUP);
     if (split.part == 1) return launches;
     if (!brute) {
         mark(K_EXPAND, 0);
@@ -2294,6 +2658,9 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
         launches++;
     }
     if (recheck) {
+        mark(K_REFINE, 0);
+        k_refine<<<n_sm * 2, 256, 0, st>>>(a);
+        mark(K_REFINE, 1);
         mark(K_RECHECK_FILTER, 0);
         k_recheck_filter<<<n_sm * 2, 256, 0, st>>>(a);
         mark(K_RECHECK_FILTER, 1);
@@ -2303,7 +2670,7 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
         mark(K_RECHECK_PAIRS, 0);
         k_recheck_pairs<<<n_sm * 2, RECHECK_BLOCK, 0, st>>>(a);
         mark(K_RECHECK_PAIRS, 1);
-        launches += 3;
+        launches += 4;
     }
     int dec_blocks = (int)std::min<uint32_t>((a.n_rays_total + 255) / 256, (uint32_t)n_sm * 8);
     mark(K_DECODE, 0);
@@ -2398,17 +2765,15 @@ extern "C" grca_status grca_cast_noalloc(const grca_sensor_desc* d, const float*
     using namespace grca;
     if (!d || !d->elev_rad || !out_dist || !out_tri || (!tris && n_tris)) return GRCA_ERR_INVALID_ARG;
     if (flags & ~(uint32_t)GRCA_CAST_CULL_BACKFACE) return GRCA_ERR_INVALID_ARG;
-    if (d->n_channels < 1 || d->n_rays < 1 || !(d->dtheta > 0.0) || !std::isfinite(d->theta0) ||
-        d->n_rays * d->dtheta > 2 * M_PI + 1e-9 || !(d->d_min >= 0.0) || !(d->d_max >= d->d_min))
-        return GRCA_ERR_INVALID_ARG;
-    for (uint32_t j = 0; j < d->n_channels && j < NOALLOC_MAX_CHANNELS; ++j)
-        if (!std::isfinite(d->elev_rad[j]) || std::fabs(d->elev_rad[j]) >= M_PI / 2 ||
-            (j > 0 && !(d->elev_rad[j] > d->elev_rad[j - 1])))
-            return GRCA_ERR_INVALID_ARG;
     // sizes beyond the fixed scratch array are rejected
     if (d->n_channels > NOALLOC_MAX_CHANNELS || d->n_rays > NOALLOC_MAX_AZIMUTH ||
         (uint64_t)d->n_channels * d->n_rays > NOALLOC_MAX_RAYS)
         return GRCA_ERR_CAPACITY;
+    // every check of grca_create_sensor (orthonormal axes, finite origin,
+    // |theta0| <= 4 pi, finite d_min, ...), then the vertex buffer's alignment:
+    // the culling kernel loads it as float4
+    if (!sensor_desc_valid(d)) return GRCA_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(tris) & 15u) return GRCA_ERR_INVALID_ARG;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return GRCA_ERR_CUDA;
     unsigned char* scratch = nullptr;
@@ -2488,6 +2853,9 @@ extern "C" grca_status grca_cast_noalloc(const grca_sensor_desc* d, const float*
     a.out_tri = out_tri;
     LaunchCfg cfg;
     cudaStream_t st = (cudaStream_t)stream;
+    // an error left by an earlier, unrelated launch is cleared here, so that
+    // the status below reports this call's launches only
+    (void)cudaGetLastError();
     int blocks = (int)std::min<uint32_t>((a.n_rays_total + 255) / 256, (uint32_t)n_sm * 8);
     k_noalloc_prepare<<<std::max(blocks, 1), 256, 0, st>>>(P, scratch);
     size_t smem = cull_smem_bytes(a, cfg);

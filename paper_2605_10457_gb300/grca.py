@@ -50,7 +50,9 @@ class grca_stats(ctypes.Structure):
                                                "chunks", "tests", "hits", "uncertain", "ties", "flagged_rays",
                                                "recheck_pairs", "group_culled", "bvh_node_visits", "bvh_tests",
                                                "n_rays")] + \
-               [("device_error", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+               [("device_error", ctypes.c_uint32), ("reserved", ctypes.c_uint32)] + \
+               [(f"{w}_{c}", ctypes.c_uint64) for w in ("queued", "kept")
+                for c in ("edge", "t", "range", "orient", "tie")] + [("t_refined", ctypes.c_uint64)]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}

@@ -1,0 +1,222 @@
+"""Per-config error of the GPU path against the FP64 oracle (test
+infrastructure: it runs the oracle).
+
+Two steps, so that the slow oracle pass can run on any CPU while the GPU is
+used for a few minutes only:
+
+  python tests/accuracy_report.py dump  --out gpu_results.npz   # on a GPU machine
+  python tests/accuracy_report.py grade --inp gpu_results.npz \
+      --md profiles/accuracy.md --json profiles/accuracy.json   # on any CPU
+
+`dump` casts every checked frame of every workload twice through the
+library, in the benchmark's launch configuration (autotuned, CUDA-graph
+replay): the FP32 test with the FP64 re-test, and the FP32 test alone.  It
+keeps the results of a ray sample: 8192 stratified rays per frame (every
+channel of every sensor, evenly strided azimuths, a seeded phase), plus every
+stress-aimed ray of c5, plus all rays of c1.  Checked frames: c2-c4 at the
+first, middle and last frame, c4 also at 100, 50 and 10 m maximum range, c5
+at every 10th frame of its 60-frame stream.  It also stores a SHA-256 of each
+frame's triangles.
+
+`grade` regenerates each frame from the same seeds, checks the hash (the
+scene generator gives the same bits on x86 and Arm), runs the FP64 oracle
+on the sample and grades both results with one rule, the stated tolerances:
+id equal, or in the oracle's near-tie set (1e-6 relative), or within 1e-7 rad
+of the GPU triangle whose plane distance is within 1e-6 of the best;
+distance within 1e-5 relative; hit/miss equal except within 1e-12 rad of
+the triangle's boundary.  The FP32-only result gets no other exemption: its
+counts are the error rates of the plain path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+sys.path.insert(0, ROOT)
+sys.path.insert(0, HERE)
+
+N_SAMPLE = 8192
+
+
+def plan():
+    """(config, d_max or None, frames) of every checked workload."""
+    p = [("c1", None, [0])]
+    for cfg in ("c2", "c3"):
+        p.append((cfg, None, [0, 25, 49]))
+    for dm in (None, 100.0, 50.0, 10.0):
+        p.append(("c4", dm, [0, 25, 49]))
+    p.append(("c5", None, [0, 10, 20, 30, 40, 50]))
+    return p
+
+
+def scene_for(cfg, d_max):
+    from scenes import make_config
+    sc = make_config(cfg)
+    if d_max is not None:
+        for s in sc.sensors:
+            s.d_min, s.d_max = 0.05, float(d_max)
+    return sc
+
+
+def sample_rays(sc, cfg, frame):
+    from grading import stratified_rays
+    if cfg == "c1":
+        return np.arange(sc.n_rays, dtype=np.int64)
+    rays = stratified_rays(sc.sensors, N_SAMPLE // len(sc.sensors), seed=1000 + frame)
+    stress = getattr(sc, "stress_rays", None)
+    if stress is not None and len(stress):
+        rays = np.unique(np.concatenate([rays, np.asarray(stress, np.int64)]))
+    return rays.astype(np.int64)
+
+
+def tri_hash(tris):
+    return hashlib.sha256(np.ascontiguousarray(tris, np.float32).tobytes()).hexdigest()[:32]
+
+
+def key(cfg, d_max, frame):
+    return f"{cfg}|{'inf' if d_max is None else f'{d_max:g}'}|{frame}"
+
+
+def dump(out_path):
+    import torch
+    from paper_2605_10457_gb300 import grca
+    res = {}
+    meta = {}
+    for cfg, d_max, frames in plan():
+        sc = scene_for(cfg, d_max)
+        c = grca.Caster(0, big_pair_capacity=16 << 20, chunk_capacity=64 << 20, recheck_capacity=32 << 20)
+        ids = [c.add_sensor(s) for s in sc.sensors]
+        for fi, f in enumerate(frames):
+            tris = np.ascontiguousarray(sc.tris(f))
+            c.upload(tris)
+            out = c.outputs(ids)
+            fl = grca.CAST_FP64_RECHECK
+            if fi == 0:
+                c.autotune(ids, fl, out)
+            rays = sample_rays(sc, cfg, f)
+            idx = torch.from_numpy(rays).cuda()
+            k = key(cfg, d_max, f)
+            for name, flags in (("recheck", fl), ("fp32", 0)):
+                c.cast(ids, flags | grca.CAST_GRAPH, out)
+                c.cast(ids, flags | grca.CAST_GRAPH, out)   # replay
+                torch.cuda.synchronize()
+                st = c.stats()
+                res[f"{k}|{name}|t"] = out[0][idx].cpu().numpy()
+                res[f"{k}|{name}|id"] = out[1][idx].cpu().numpy().view(np.uint32)
+                meta[f"{k}|{name}"] = {s_: st[s_] for s_ in ("n_rays", "flagged_rays", "hits", "queued_t", "t_refined",
+                                                             "kept_edge", "kept_t", "kept_tie", "device_error")}
+            res[f"{k}|rays"] = rays
+            meta[k] = {"hash": tri_hash(tris), "triangles": int(tris.shape[0]),
+                       "launch_config": c.launch_config(ids, fl)}
+            print(k, len(rays), meta[f"{k}|recheck"], flush=True)
+        c.close()
+    np.savez_compressed(out_path, meta=json.dumps(meta), **res)
+
+
+def grade(inp, md_path, json_path, threads, only=None):
+    import oracle
+    from grading import grade as grade_rule, oracle_two_pass, summary
+    z = np.load(inp)
+    meta = json.loads(str(z["meta"]))
+    rows = []
+    for cfg, d_max, frames in plan():
+        if only and cfg not in only:
+            continue
+        sc = scene_for(cfg, d_max)
+        orc = oracle.Oracle(sc.sensors)
+        stress = getattr(sc, "stress_rays", None)
+        stress = np.zeros(0, np.int64) if stress is None else np.asarray(stress, np.int64)
+        for f in frames:
+            k = key(cfg, d_max, f)
+            if f"{k}|rays" not in z:
+                continue
+            tris = np.ascontiguousarray(sc.tris(f))
+            assert tri_hash(tris) == meta[k]["hash"], f"{k}: the regenerated frame differs from the GPU's"
+            rays = z[f"{k}|rays"]
+            results = {n: (z[f"{k}|{n}|t"], z[f"{k}|{n}|id"]) for n in ("recheck", "fp32")}
+            t0 = time.time()
+            ref = oracle_two_pass(orc, tris, rays, list(results.values()), n_threads=threads)
+            row = {"workload": k, "config": cfg, "d_max": d_max, "frame": f, "rays": int(len(rays)),
+                   "stress_rays": int(np.isin(rays, stress).sum()),
+                   "oracle_s": time.time() - t0, "triangles": int(tris.shape[0])}
+            for n, (gt, gid) in results.items():
+                g = grade_rule(orc, tris, ref, gt, gid)
+                row[n] = summary(g, ref, gt, gid)
+                row[n]["stats"] = meta[f"{k}|{n}"]
+            rows.append(row)
+            print(k, {n: row[n]["errors"] for n in results}, f"{row['oracle_s']:.0f} s", flush=True)
+            with open(json_path, "w") as fh:
+                json.dump(rows, fh, indent=1)
+    write_md(rows, md_path, inp)
+
+
+def write_md(rows, md_path, inp):
+    L = ["# Error against the FP64 oracle, per workload", "",
+         "Each row is one checked frame: the GPU results of a ray sample (8192 stratified rays, every stress-aimed ray "
+         "of c5, all rays of c1) graded against the FP64 brute-force oracle with one rule for both paths: id equal, or "
+         "in the oracle's near-tie set (1e-6 relative), or within 1e-7 rad of the GPU triangle whose plane distance is "
+         "within 1e-6 relative of the best; distance within 1e-5 relative; hit/miss equal except within 1e-12 rad of "
+         "the triangle's boundary.", "",
+         "- **FP32 + FP64 re-test**: the benchmark's exact path (autotuned launch configuration, CUDA-graph replay).",
+         "- **FP32 only**: the same cast without the re-test; its errors are the plain path's mismatch rates.",
+         "- *tie* / *edge*: rays whose GPU id differs from the oracle's but is accepted by the near-tie rule or the "
+         "shared-edge rule.",
+         "- Distance error: relative, over rays where both report the same triangle.",
+         "- Flagged: rays the FP32 pass sent to the FP64 re-test in that frame (whole frame).", "",
+         "Commands (the first on a GB300, the second on any CPU; the scene generator gives the same triangles on both, "
+         "checked by hash):", "", "```",
+         "python tests/accuracy_report.py dump --out gpu_results.npz",
+         "python tests/accuracy_report.py grade --inp gpu_results.npz --md profiles/accuracy.md "
+         "--json profiles/accuracy.json", "```", "",
+         "| workload (config, d_max, frame) | rays | oracle hits | FP32+re-test errors (id / hit-miss / dist) | "
+         "tie / edge accepted | max / median dist err | FP32-only errors (id / hit-miss / dist) | FP32-only error rate | "
+         "FP32-only max dist err | flagged rays (frame) |",
+         "|---|---|---|---|---|---|---|---|---|---|"]
+    tot = {"recheck": 0, "fp32": 0, "rays": 0}
+    for r in rows:
+        a, b = r["recheck"], r["fp32"]
+        tot["recheck"] += a["errors"]
+        tot["fp32"] += b["errors"]
+        tot["rays"] += r["rays"]
+        fl = a["stats"]["flagged_rays"]
+        nr = a["stats"]["n_rays"]
+        L.append(f"| {r['workload']} | {r['rays']:,}" + (f" ({r['stress_rays']} stress)" if r["stress_rays"] else "") +
+                 f" | {a['oracle_hits']:,} | {a['errors']} ({a['id_mismatch']} / {a['hit_miss']} / {a['dist_bad']}) | "
+                 f"{a['tie_accepted']} / {a['edge_accepted']} | {a['max_rel_dist_err']:.2e} / "
+                 f"{a['median_rel_dist_err']:.1e} | {b['errors']} ({b['id_mismatch']} / {b['hit_miss']} / "
+                 f"{b['dist_bad']}) | {100 * b['error_rate']:.3f} % | {b['max_rel_dist_err']:.2e} | "
+                 f"{fl:,} ({100 * fl / max(1, nr):.2f} %) |")
+    L += ["", f"Total: {tot['rays']:,} graded rays; FP32 + FP64 re-test errors: {tot['recheck']}; FP32-only errors: "
+              f"{tot['fp32']}.", ""]
+    with open(md_path, "w") as fh:
+        fh.write("\n".join(L))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("mode", choices=["dump", "grade", "md"])
+    ap.add_argument("--out", default="gpu_results.npz")
+    ap.add_argument("--inp", default="gpu_results.npz")
+    ap.add_argument("--md", default=os.path.join(ROOT, "profiles", "accuracy.md"))
+    ap.add_argument("--json", default=os.path.join(ROOT, "profiles", "accuracy.json"))
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--only", nargs="*", default=None)
+    args = ap.parse_args()
+    if args.mode == "dump":
+        dump(args.out)
+    elif args.mode == "grade":
+        grade(args.inp, args.md, args.json, args.threads or (os.cpu_count() or 1), args.only)
+    else:
+        write_md(json.load(open(args.json)), args.md, args.inp)
+
+
+if __name__ == "__main__":
+    main()

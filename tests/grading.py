@@ -88,3 +88,46 @@ def stratified_rays(sensors, n_per_sensor: int, seed: int = 0) -> np.ndarray:
             out.append(off + int(j) * s.n_rays + i)
         off += s.n_channels * s.n_rays
     return np.unique(np.concatenate(out).astype(np.int64))
+
+
+def oracle_two_pass(orc: "oracle.Oracle", tris: np.ndarray, rays: np.ndarray, gpu_results, n_threads=None,
+                    plain_ref: dict = None) -> dict:
+    """Oracle reference for grading several GPU results on the same rays at the
+    cost of one plain oracle pass: the closest hit of every ray first, then
+    the near-tie data (runner-up, tie set) only for the rays where some GPU
+    result differs from it in id or in hit/miss (the only rays where grade()
+    reads that data).  gpu_results: list of (t, id) arrays over `rays`;
+    plain_ref: the first pass, if it was already run."""
+    ref = dict(plain_ref) if plain_ref is not None else oracle.cast(orc, tris, rays, n_threads=n_threads)
+    oid = ref["id"].astype(np.int64)
+    need = np.zeros(rays.shape[0], bool)
+    for _, gid in gpu_results:
+        need |= (np.asarray(gid).astype(np.int64) & 0xFFFFFFFF) != oid
+    ref["second"] = np.full(rays.shape[0], np.nan)
+    ref["n_ties"] = np.ones(rays.shape[0], np.uint32)
+    ref["tie_ids"] = np.full((rays.shape[0], oracle.MAX_TIES), oracle.NO_HIT, np.uint32)
+    ref["tie_ids"][:, 0] = ref["id"]
+    if need.any():
+        sub = oracle.cast(orc, tris, rays[need], ties=True, n_threads=n_threads)
+        assert np.array_equal(sub["id"], ref["id"][need]) and np.array_equal(sub["t"], ref["t"][need])
+        ref["second"][need] = sub["second"]
+        ref["n_ties"][need] = sub["n_ties"]
+        ref["tie_ids"][need] = sub["tie_ids"]
+    ref["tie_pass_rays"] = int(need.sum())
+    return ref
+
+
+def summary(g: dict, ref: dict, gpu_t: np.ndarray, gpu_id: np.ndarray) -> dict:
+    """Per-ray error statement of one graded result: counts by rule, and the
+    relative distance error over the rays where both hit the same triangle."""
+    gt = np.asarray(gpu_t, np.float64)
+    gid = np.asarray(gpu_id).astype(np.int64) & 0xFFFFFFFF
+    same = (gid == ref["id"].astype(np.int64)) & (gid != oracle.NO_HIT)
+    rel = np.abs(gt[same] - ref["t"][same]) / ref["t"][same] if same.any() else np.zeros(0)
+    n = max(1, g["n"])
+    return {"rays": g["n"], "oracle_hits": g["hits"], "id_mismatch": g["id_mismatch"], "hit_miss": g["hit_miss"],
+            "dist_bad": g["dist_bad"], "errors": g["errors"], "error_rate": g["errors"] / n,
+            "tie_accepted": g["tie_accepted"], "edge_accepted": g["edge_accepted"],
+            "silhouette_accepted": g["silhouette_accepted"],
+            "max_rel_dist_err": float(rel.max()) if rel.size else 0.0,
+            "median_rel_dist_err": float(np.median(rel)) if rel.size else 0.0}

@@ -128,6 +128,92 @@ def test_tiny_random_scenes_brute_equals_culled():
         assert g["errors"] == 0, (seed, g)
 
 
+def test_far_from_the_world_origin_brute_equals_culled():
+    """Sensors and scene about 3 km from the world origin, where the FP32
+    origin's low part o_lo reaches 1e-4 m: the elevation and range culls
+    widen their bounds by |o_lo| instead of subtracting it per vertex, and
+    must still keep every hit (culled == no-cull, bit for bit), with and
+    without range limits and for tilted sensors."""
+    from paper_2605_10457_gb300.grca import CAST_BRUTE, CAST_FP64_RECHECK
+    off = np.array([2345.678, -1987.654, 12.345])
+    for seed in range(3):
+        tris = (tiny_scene(seed, n_tris=300, extent=6.0).astype(np.float64) + off).astype(np.float32)
+        sens = [make_sensor(off + (0.0, 0.0, 0.5), channels="c32", n_rays=720),
+                make_sensor(off + (0.3, -0.2, 1.0), yaw=0.4, channels="c64", n_rays=512, fov_deg=180.0,
+                            d_min=0.3, d_max=4.0),
+                make_sensor(off + (-0.5, 0.1, 0.2), yaw=-1.0, channels="uniform16", n_rays=360, pitch=0.3,
+                            roll=-0.2, d_max=7.0)]
+        c = _caster()
+        ids = [c.add_sensor(s) for s in sens]
+        c.upload(tris)
+        for fl in (0, CAST_FP64_RECHECK):
+            d0, t0 = _cast(c, ids, fl)
+            d1, t1 = _cast(c, ids, fl | CAST_BRUTE)
+            assert np.array_equal(t0, t1), (seed, fl, np.nonzero(t0 != t1)[0][:8])
+        assert (t0 != 0xFFFFFFFF).sum() > 1000
+        sc = type("S", (), {"sensors": sens})
+        g = _check(sc, tris, d0, t0)
+        assert g["errors"] == 0, (seed, g)
+
+
+def _grid_wall(x0, x1, z0, z1, y, nx, nz, yaw):
+    """Vertical wall y = const (before a yaw about z), nx x nz quads, shared edges."""
+    xs, zs = np.linspace(x0, x1, nx + 1), np.linspace(z0, z1, nz + 1)
+    c, s_ = math.cos(yaw), math.sin(yaw)
+    P = np.array([[[x * c - y * s_, x * s_ + y * c, z] for x in xs] for z in zs])
+    tris = []
+    for a in range(nz):
+        for b in range(nx):
+            p00, p01, p10, p11 = P[a, b], P[a, b + 1], P[a + 1, b], P[a + 1, b + 1]
+            tris += [[p00, p01, p11], [p00, p11, p10]]
+    return np.asarray(tris, np.float32)
+
+
+def test_grazing_hits_get_exact_distances_without_the_fp64_queue():
+    """Rays that meet long yawed walls and the ground at a few degrees of
+    incidence: the FP32 distance bound exceeds the accepted one there, and
+    the double-float re-evaluation of t must settle every such hit (no entry
+    of cause t kept for the FP64 re-test), with distances within 1e-6
+    relative of the FP64 oracle and zero errors under the grading rule."""
+    from paper_2605_10457_gb300.grca import CAST_FP64_RECHECK
+    walls = np.concatenate([_grid_wall(-40.0, 300.0, 0.0, 4.0, 3.0, 170, 4, 0.013),
+                            _grid_wall(-40.0, 300.0, 0.0, 4.0, -5.0, 170, 4, -0.021)])
+    xs = np.linspace(-60.0, 320.0, 39)
+    ys = np.linspace(-40.0, 40.0, 9)
+    ground = []
+    for a_ in range(len(xs) - 1):
+        for b in range(len(ys) - 1):
+            p = [(xs[a_], ys[b], 0.0), (xs[a_ + 1], ys[b], 0.0), (xs[a_ + 1], ys[b + 1], 0.0), (xs[a_], ys[b + 1], 0.0)]
+            ground += [[p[0], p[1], p[2]], [p[0], p[2], p[3]]]
+    # the whole scene turned by psi about z, the sensors pitched and rolled a
+    # little: no axis-aligned direction is left to make the FP32 bound small
+    psi = 0.7
+    cz, sz = math.cos(psi), math.sin(psi)
+    R = np.array([[cz, -sz, 0.0], [sz, cz, 0.0], [0.0, 0.0, 1.0]])
+    tris = np.concatenate([walls, np.asarray(ground, np.float32)]).astype(np.float64) @ R.T
+    tris = tris.astype(np.float32)
+    sens = [make_sensor(R @ (0.0, 0.0, 1.5), yaw=psi + 0.0021, channels="c64", n_rays=2048, fov_deg=30.0,
+                        pitch=0.05, roll=-0.03),
+            make_sensor(R @ (5.0, -1.0, 2.0), yaw=psi - 0.0137, channels="c32", n_rays=1024, fov_deg=20.0,
+                        pitch=0.02, roll=0.04)]
+    c = _caster()
+    ids = [c.add_sensor(s) for s in sens]
+    c.upload(tris)
+    d, t = _cast(c, ids, CAST_FP64_RECHECK)
+    st = c.stats()
+    assert st["device_error"] == 0
+    assert st["queued_t"] > 200 and st["t_refined"] == st["queued_t"] and st["kept_t"] == 0, st
+    sc = type("S", (), {"sensors": sens})
+    orc = oracle.Oracle(sens)
+    ref = oracle.cast(orc, tris, None, ties=True)
+    g = grade(orc, tris, ref, d, t)
+    assert g["errors"] == 0, g
+    same = (t.astype(np.int64) == ref["id"].astype(np.int64)) & (t != 0xFFFFFFFF)
+    assert same.sum() > 20000
+    rel = np.abs(d[same] - ref["t"][same]) / ref["t"][same]
+    assert rel.max() <= 1e-6, rel.max()
+
+
 def test_candidate_spans_cover_every_exact_hit():
     """Every (ray, triangle) pair that the FP64 oracle finds hitting must be
     among the candidates the culling passes emit (debug dump)."""
