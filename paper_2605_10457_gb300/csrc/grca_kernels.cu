@@ -1590,6 +1590,14 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
         }
         if (fill + 32 * ns > SURV_BUF) flush_survivors(a, W, fill, lane, a.n_sensors);
         stage_tris(a, base, cnt, W.tri, lane);
+        {
+            // the warp's next tile into L2 while this one is worked on (9 lines of 128 B)
+            const uint32_t nb = base + n_warps * 32;
+            if (nb < a.n_tris && lane < 9 && 32u * lane < 9u * min(32u, a.n_tris - nb)) {
+                const float* pp = a.tris + 9ull * nb + 32 * lane;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pp));
+            }
+        }
         bool valid = lane < cnt && lane >= skip;
         const float* t9 = W.tri + 9 * (valid ? lane : 0);
         const V3 v[3] = {{t9[0], t9[1], t9[2]}, {t9[3], t9[4], t9[5]}, {t9[6], t9[7], t9[8]}};
@@ -1639,18 +1647,43 @@ struct CullBWarpSmem {
     uint32_t cnt[8];             // live, cand, inl, big, tests, hits, unc, ties
 };
 
+// Tie check of a committed certain hit against the key its atomicMin
+// returned (FP32 + re-test mode): a different triangle within the tie band
+// queues both for the FP64 re-test.
+__device__ __forceinline__ void tie_check(const CastArgs& a, uint32_t g, uint32_t tri, float t, unsigned long long old,
+                                          uint32_t& n_ties) {
+    const uint32_t oid = (uint32_t)old;
+    if (oid != NO_HIT && oid != tri) {
+        const float told = __uint_as_float((uint32_t)(old >> 32));
+        if (fabsf(__fsub_rn(t, told)) <= __fmul_rn(BETA, fmaxf(t, told))) {
+            push_recheck(a, g, tri, __fmul_rn(t, 1.f - TAU_T), UC_TIE);
+            push_recheck(a, g, oid, __fmul_rn(told, 1.f - TAU_T), UC_TIE);
+            n_ties++;
+        }
+    }
+}
+
 // Setup, first test and cooperative candidate expansion of the warp's
-// pending live pairs W.pend[0, np), np <= 32, one pair per lane.  Called by
-// the whole warp.
+// pending live pairs W.pend[0, np), np <= 32: one pair per lane gets its
+// test setup into shared memory and tests its first candidate, then the warp
+// expands all other candidates of the np pairs together, one candidate per
+// lane per round (owner found from the warp's prefix sums).  The tie check of
+// a commit waits for the next round, so that the atomicMin's returned key
+// arrives while that round is tested.  Called by the whole warp.
 template <bool RECHECK>
 __device__ __forceinline__ void cull_b_test_pairs(const CastArgs& a, const CullSmem& M, CullBWarpSmem& W, uint32_t np,
                                                   uint32_t lane, bool dump, uint32_t& c_hits, uint32_t& c_unc,
                                                   uint32_t& c_ties) {
-    uint32_t ncand = 0, hit0 = 0, tested0 = 0;
+    uint32_t ncand = 0, tested0 = 0;
+    // a committed hit waiting for its tie check (first the setup lane's own test)
+    bool pend = false;
+    uint32_t pg = 0, ptri = 0;
+    float pt = 0.f;
+    unsigned long long pold = 0ull;
     if (lane < np) {
         const uint4 e = W.pend[lane];
         const uint32_t tri = e.x, meta = e.y, my_r0 = e.z, nc = e.w;
-        const uint32_t sn = meta >> 26, j_lo = meta & 1023u;
+        const uint32_t sn = meta >> 26;
         const SensorDev& S = M.sens[sn];
         float t9[9];
         const float* src = a.tris + 9ull * tri;
@@ -1673,20 +1706,42 @@ __device__ __forceinline__ void cull_b_test_pairs(const CastArgs& a, const CullS
             W.meta[lane] = meta;
             W.r0[lane] = my_r0;
             W.inv[lane] = __frcp_ru((float)((meta >> 10) & 0xFFFFu));
-            // the pair's first candidate is tested here by its own lane;
-            // the remaining ones are expanded cooperatively below
+            // the pair's first candidate is tested here by its own lane
+            const uint32_t j_lo = meta & 1023u;
             const uint32_t g = S.ray_off + j_lo * S.n_rays + my_r0;
             const unsigned long long cur = __ldcg(&a.keys[g]);
             V3 d = ray_dir(M.ch[S.ch_loc + j_lo], __ldg(&a.az_sc[S.az_off + my_r0]));
             float t, terr;
-            int res = test_fp32<RECHECK>(SetupSoA{&W.st[0][0], lane}, S, d, t, terr);
+            const int res = test_fp32<RECHECK>(SetupSoA{&W.st[0][0], lane}, S, d, t, terr);
             if (dump) dump_candidate(a, g, tri);
-            hit0 = commit_pre<RECHECK>(a, g, tri, res, t, terr, cur, c_unc, c_ties);
             tested0 = 1;
             ncand = nc - 1;
+            if (res != T_MISS) {
+                const float tcur = __uint_as_float((uint32_t)(cur >> 32));
+                if (is_uncertain(res)) {
+                    const bool t_ok = terr < 0.25f && t > 0.f;
+                    const float t_lo = __fmul_rn(t, __fsub_rn(1.f, terr));
+                    if (!(t_ok && t_lo > __fmul_rn(tcur, 1.f + BETA))) {
+                        push_recheck(a, g, tri, t_ok ? t_lo : 0.f, (uint32_t)(res - T_UNCERTAIN));
+                        c_unc++;
+                    }
+                } else {
+                    c_hits++;
+                    const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | tri;
+                    if (!RECHECK) {
+                        if (key < cur) atomicMin(&a.keys[g], key);
+                    } else if (!(t > __fmul_rn(tcur, 1.f + BETA))) {
+                        pold = atomicMin(&a.keys[g], key);
+                        pend = true;
+                        pg = g;
+                        ptri = tri;
+                        pt = t;
+                    }
+                }
+            }
         }
     }
-    // warp prefix sum of the inline candidate counts
+    // warp prefix sum of the candidate counts
     uint32_t incl = ncand;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -1698,11 +1753,10 @@ __device__ __forceinline__ void cull_b_test_pairs(const CastArgs& a, const CullS
     const uint32_t nz = __ballot_sync(0xffffffffu, ncand > 0);   // lanes that own candidates, in order
     if (ncand > 0) W.own[__popc(nz & ((1u << lane) - 1u))] = lane;
     {
-        const uint32_t s_t0 = __reduce_add_sync(0xffffffffu, tested0), s_h0 = __reduce_add_sync(0xffffffffu, hit0);
+        const uint32_t s_t0 = __reduce_add_sync(0xffffffffu, tested0);
         if (lane == 0) {
             W.cnt[2] += total + s_t0;
             W.cnt[4] += total + s_t0;
-            W.cnt[5] += s_h0;
         }
     }
     __syncwarp();
@@ -1720,10 +1774,14 @@ __device__ __forceinline__ void cull_b_test_pairs(const CastArgs& a, const CullS
         const uint32_t tri = W.tri[own & 31u];
         const float inv = W.inv[own & 31u];
         const uint32_t cc = c0 + lane;
+        int res = T_MISS;
+        float t = 0.f, terr = 0.f;
+        uint32_t g = 0;
+        unsigned long long cur = 0ull;
         if (cc < total) {
             const uint32_t nr = (meta >> 10) & 0xFFFFu;
             const uint32_t sn = meta >> 26;
-            uint32_t idx = cc - o_excl + 1;   // candidate 0 was tested by the owner lane
+            const uint32_t idx = cc - o_excl + 1;   // candidate 0 was tested by the owner lane
             // quotient from the rounded-up reciprocal, then one correction
             // step in each direction (enough for idx < 2^24, where (float)idx
             // is exact); a quotient still off (larger spans of the no-cull
@@ -1743,15 +1801,39 @@ __device__ __forceinline__ void cull_b_test_pairs(const CastArgs& a, const CullS
             const uint32_t j = (meta & 1023u) + jo;
             uint32_t i = r0o + io;
             if (i >= S.n_rays) i -= S.n_rays;
-            const uint32_t g = S.ray_off + j * S.n_rays + i;
-            const unsigned long long cur = __ldcg(&a.keys[g]);   // issued before the test arithmetic
+            g = S.ray_off + j * S.n_rays + i;
+            cur = __ldcg(&a.keys[g]);   // issued before the test arithmetic
             V3 d = ray_dir(M.ch[S.ch_loc + j], __ldg(&a.az_sc[S.az_off + i]));
-            float t, terr;
-            int res = test_fp32<RECHECK>(SetupSoA{&W.st[0][0], own & 31u}, S, d, t, terr);
+            res = test_fp32<RECHECK>(SetupSoA{&W.st[0][0], own & 31u}, S, d, t, terr);
             if (dump) dump_candidate(a, g, tri);
-            c_hits += commit_pre<RECHECK>(a, g, tri, res, t, terr, cur, c_unc, c_ties);
+        }
+        if (RECHECK && pend) tie_check(a, pg, ptri, pt, pold, c_ties);
+        pend = false;
+        if (res == T_MISS) continue;
+        const float tcur = __uint_as_float((uint32_t)(cur >> 32));
+        if (is_uncertain(res)) {
+            // a re-test can only change the result if it may beat the current best
+            const bool t_ok = terr < 0.25f && t > 0.f;
+            const float t_lo = __fmul_rn(t, __fsub_rn(1.f, terr));
+            if (!(t_ok && t_lo > __fmul_rn(tcur, 1.f + BETA))) {
+                push_recheck(a, g, tri, t_ok ? t_lo : 0.f, (uint32_t)(res - T_UNCERTAIN));
+                c_unc++;
+            }
+            continue;
+        }
+        c_hits++;
+        const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | tri;
+        if (!RECHECK) {
+            if (key < cur) atomicMin(&a.keys[g], key);
+        } else if (!(t > __fmul_rn(tcur, 1.f + BETA))) {
+            pold = atomicMin(&a.keys[g], key);
+            pend = true;
+            pg = g;
+            ptri = tri;
+            pt = t;
         }
     }
+    if (RECHECK && pend) tie_check(a, pg, ptri, pt, pold, c_ties);
     __syncwarp();
 }
 

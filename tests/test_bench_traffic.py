@@ -35,8 +35,8 @@ def test_traffic_null_once_the_kernels_change(monkeypatch, tmp_path):
 def test_committed_capture_is_well_formed():
     d = json.load(open(os.path.join(ROOT, "profiles", "traffic_c5.json")))
     assert len(d["kernels_sha256"]) == 64 and d["command"].startswith("ncu ")
-    for k in ("k_cull_a", "k_cull_b"):
-        e = d["kernels"][k]
+    assert d["kernels"]
+    for k, e in d["kernels"].items():
         assert e["dram_bytes_per_launch"] == e["dram_bytes_read"] + e["dram_bytes_write"] > 0
 
 
