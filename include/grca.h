@@ -234,6 +234,43 @@ grca_status grca_update_vertices(grca_ctx* ctx, const float* xyz, uint32_t first
 grca_status grca_cast(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_sensors, float* out_dist,
                       uint32_t* out_tri, uint32_t flags, void* stream);
 
+/* Triangle-sharded casts (several GPUs, each holding a slice of the
+ * triangles).  The closest hit over the union of the slices is the minimum,
+ * over the slices, of each slice's closest hit (Sec. 1.1, Eq. brute: the
+ * result is a minimum over triangles), so a frame is cast per slice and the
+ * per-ray (distance, id) keys are combined by a u64 MIN across the GPUs
+ * (the caller's collective; keys are < 2^63, so a signed int64 MIN gives the
+ * same result).  Protocol per frame, the same sensors and flags on every
+ * shard, each shard holding triangles with global ids tri_base + local id:
+ *   1. grca_cast_shard: the FP32 pass over this GPU's slice (with the
+ *      double-float re-evaluation of t); keys_out receives one u64 key per
+ *      ray, (FP32 bits of t) << 32 | global triangle id, 0x7F800000FFFFFFFF
+ *      for a miss.
+ *   2. keys_min = MIN over the shards of those keys.  Without
+ *      GRCA_CAST_FP64_RECHECK, keys_min is final: go to 5.
+ *   3. grca_flag_shard: the FP64 re-test's filter against keys_min; flags_out
+ *      receives one byte per ray, 1 where this shard holds a queued candidate
+ *      that may beat or tie keys_min, or an FP32 winner other than keys_min's
+ *      triangle within the tie band of it.  flags_any = MAX over the shards.
+ *   4. grca_resolve_shard: every ray with flags_any set is settled in FP64 by
+ *      each shard holding a candidate within the tie band (the shard of
+ *      keys_min's triangle included); keys_out receives this shard's keys,
+ *      the FP64 ones where settled.  keys_final = MIN over the shards.
+ *   5. grca_decode_keys (any shard): distances and global ids of the keys.
+ * The result equals a single-GPU cast of the whole triangle set with the
+ * same flags: the re-test sees the same candidates.
+ * Flags: as grca_cast except GRAPH, BRUTE, DUMP_CANDIDATES and HOST_ASYNC
+ * (GRCA_ERR_INVALID_ARG).  Key arrays (int64 / u64) and flag arrays (one
+ * byte) are DEVICE arrays of the cast's ray count.  Steps 3-5 use the work
+ * buffers of the context's last grca_cast_shard (GRCA_ERR_NOT_READY without
+ * one; step 4 also needs step 3, and reads keys_min again: keep it until
+ * then); no other cast may run on the context in between. */
+grca_status grca_cast_shard(grca_ctx* ctx, const int32_t* sensor_ids, uint32_t n_sensors, uint32_t tri_base,
+                            uint64_t* keys_out, uint32_t flags, void* stream);
+grca_status grca_flag_shard(grca_ctx* ctx, const uint64_t* keys_min, uint8_t* flags_out, void* stream);
+grca_status grca_resolve_shard(grca_ctx* ctx, const uint8_t* flags_any, uint64_t* keys_out, void* stream);
+grca_status grca_decode_keys(grca_ctx* ctx, const uint64_t* keys, float* out_dist, uint32_t* out_tri, void* stream);
+
 /* Same as grca_cast with HOST output arrays: the frame's vertices
  * (`xyz_dynamic`, n_dynamic triangles starting at first_dynamic, HOST;
  * pinned memory gives the fastest copy) are copied in, the results copied

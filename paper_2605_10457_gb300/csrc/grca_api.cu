@@ -68,6 +68,11 @@ struct DeviceGuard {
 
 struct grca_ctx {
     int device = 0;
+    // the last grca_cast_shard (its work buffers hold the queue that
+    // grca_resolve_shard re-tests)
+    bool shard_ready = false;
+    CastArgs shard_args{};
+    LaunchCfg shard_cfg;
     int n_sm = 152;
     grca_options opt{};
     LaunchCfg cfg;
@@ -961,6 +966,81 @@ grca_status grca_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, float* out_
     if (rs != GRCA_OK) return rs;
     ctx->last_n_rays = a.n_rays_total;
     return run_frame(ctx, a, cfg_for(ctx, a), st, (flags & GRCA_CAST_GRAPH) != 0);
+}
+
+grca_status grca_cast_shard(grca_ctx* ctx, const int32_t* ids, uint32_t n, uint32_t tri_base, uint64_t* keys_out,
+                            uint32_t flags, void* stream) {
+    if (!ctx || !keys_out) return GRCA_ERR_INVALID_ARG;
+    if (flags & (GRCA_CAST_GRAPH | GRCA_CAST_BRUTE | GRCA_CAST_DUMP_CANDIDATES | GRCA_CAST_HOST_ASYNC))
+        return GRCA_ERR_INVALID_ARG;
+    if ((uint64_t)tri_base + ctx->n_tris > 0xFFFFFFFFull) return GRCA_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CastArgs a;
+    // no decode in this stage: the key buffer stands in for the outputs
+    grca_status rs = prepare_cast(ctx, ids, n, reinterpret_cast<float*>(keys_out),
+                                  reinterpret_cast<uint32_t*>(keys_out), flags, st, a);
+    if (rs != GRCA_OK) return rs;
+    a.keys_out = reinterpret_cast<unsigned long long*>(keys_out);
+    a.tri_base = tri_base;
+    const LaunchCfg cfg = cfg_for(ctx, a);
+    a.inline_max = (uint32_t)cfg.inline_max;
+    a.chunk_rays = (uint32_t)cfg.chunk_rays;
+    FrameSplit sp;
+    sp.stage = 1;
+    ctx->last_n_rays = a.n_rays_total;
+    ctx->last_launches = ctx->pending_launches + (uint32_t)launch_frame(a, cfg, ctx->n_sm, st, nullptr, sp);
+    ctx->pending_launches = 0;
+    CK(cudaGetLastError());
+    ctx->shard_args = a;
+    ctx->shard_cfg = cfg;
+    ctx->shard_ready = true;
+    return GRCA_OK;
+}
+
+grca_status grca_flag_shard(grca_ctx* ctx, const uint64_t* keys_min, uint8_t* flags_out, void* stream) {
+    if (!ctx || !keys_min || !flags_out) return GRCA_ERR_INVALID_ARG;
+    if (!ctx->shard_ready) return GRCA_ERR_NOT_READY;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CastArgs a = ctx->shard_args;
+    a.keys_glob = reinterpret_cast<const unsigned long long*>(keys_min);
+    a.flags_out = flags_out;
+    ctx->shard_args.keys_glob = a.keys_glob;
+    FrameSplit sp;
+    sp.stage = 2;
+    ctx->last_launches = (uint32_t)launch_frame(a, ctx->shard_cfg, ctx->n_sm, st, nullptr, sp);
+    CK(cudaGetLastError());
+    return GRCA_OK;
+}
+
+grca_status grca_resolve_shard(grca_ctx* ctx, const uint8_t* flags_any, uint64_t* keys_out, void* stream) {
+    if (!ctx || !flags_any || !keys_out) return GRCA_ERR_INVALID_ARG;
+    if (!ctx->shard_ready || !ctx->shard_args.keys_glob) return GRCA_ERR_NOT_READY;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CastArgs a = ctx->shard_args;
+    a.flags_any = flags_any;
+    a.keys_out = reinterpret_cast<unsigned long long*>(keys_out);
+    FrameSplit sp;
+    sp.stage = 3;
+    ctx->last_launches = (uint32_t)launch_frame(a, ctx->shard_cfg, ctx->n_sm, st, nullptr, sp);
+    CK(cudaGetLastError());
+    return GRCA_OK;
+}
+
+grca_status grca_decode_keys(grca_ctx* ctx, const uint64_t* keys, float* out_dist, uint32_t* out_tri, void* stream) {
+    if (!ctx || !keys || !out_dist || !out_tri) return GRCA_ERR_INVALID_ARG;
+    if (!ctx->shard_ready) return GRCA_ERR_NOT_READY;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CastArgs a = ctx->shard_args;
+    a.keys = const_cast<unsigned long long*>(reinterpret_cast<const unsigned long long*>(keys));
+    a.out_dist = out_dist;
+    a.out_tri = out_tri;
+    launch_decode(a, ctx->n_sm, st);
+    CK(cudaGetLastError());
+    return GRCA_OK;
 }
 
 grca_status grca_cast_host(grca_ctx* ctx, const int32_t* ids, uint32_t n, const float* xyz_dyn, uint32_t first_dyn,

@@ -183,6 +183,15 @@ struct CastArgs {
     uint32_t surv_part;
     // elevation pass: the sensors [sens_base, sens_base + sens_count) of this launch
     uint32_t sens_base, sens_count;
+    // triangle-sharded casts: this shard's first global triangle id, the
+    // per-ray minimum over every shard's FP32 winner (keys_glob), the per-ray
+    // flags this shard exports (flags_out) and their maximum over all shards
+    // (flags_any), and the output of exported keys
+    uint32_t tri_base;
+    const unsigned long long* keys_glob;
+    uint8_t* flags_out;
+    const uint8_t* flags_any;
+    unsigned long long* keys_out;
 };
 
 struct LaunchCfg {
@@ -217,10 +226,17 @@ struct KernelMarks {
 struct FrameSplit {
     int part = 0;
     uint32_t at = 0;
+    // 0: the whole frame; stages of a triangle-sharded cast (triangle ids of
+    // exported keys offset by CastArgs::tri_base): 1 the FP32 pass (key init
+    // through k_refine) and the keys in keys_out; 2 the filter against
+    // keys_glob and the flags in flags_out; 3 the FP64 re-tests of the rays
+    // flagged in flags_any and the settled keys in keys_out (no decode)
+    int stage = 0;
 };
 int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t st,
                  const KernelMarks* marks = nullptr, FrameSplit split = FrameSplit());
 size_t cull_smem_bytes(const CastArgs& a, const LaunchCfg& cfg);  // fused k_cull
+void launch_decode(const CastArgs& a, int n_sm, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // static hierarchy (hybrid static/dynamic pipeline)

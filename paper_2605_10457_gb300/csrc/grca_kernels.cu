@@ -2330,7 +2330,8 @@ __global__ void k_recheck_filter(CastArgs a) {
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
         uint4 e = a.recheck[q];
         const unsigned long long kb = a.keys[e.x];
-        float tbest = __uint_as_float((uint32_t)(kb >> 32));
+        // a sharded cast compares against the winner over every shard
+        float tbest = __uint_as_float((uint32_t)((a.keys_glob ? a.keys_glob[e.x] : kb) >> 32));
         // entries retired by k_refine count as queued, never as kept
         const bool kept = e.y != NO_HIT && __uint_as_float(e.z) <= __fmul_rn(tbest, 1.f + BETA);
 #pragma unroll
@@ -2405,6 +2406,64 @@ __global__ void __launch_bounds__(RECHECK_BLOCK) k_recheck_pairs(CastArgs a) {
     if (lane < fill) recheck_pair(a, wb[lane]);
     kept += fill;
     if (lane == 0 && kept) atomicAdd(&a.counters[C_RECHECK], (unsigned long long)kept);
+}
+
+// ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// triangle-sharded casts (each GPU holds a slice of the triangles): the
+// closest hit over the union of the slices is the key minimum over the
+// slices' closest hits (Sec. 1.1, Eq. brute: a minimum over triangles),
+// exchanged as one per-ray u64 MIN.  The FP64 re-test of a shard runs against
+// the winner over all shards; a ray any shard flags is settled in FP64 by
+// every shard that holds a candidate within its tie band, so that the last
+// exchange (MIN of the settled keys) compares FP64 results wherever FP32
+// cannot decide.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long rebase_key(unsigned long long k, uint32_t base) {
+    const uint32_t id = (uint32_t)k;
+    return id == NO_HIT ? k : ((k & 0xFFFFFFFF00000000ull) | (unsigned long long)(id + base));
+}
+__device__ __forceinline__ float key_t(unsigned long long k) { return __uint_as_float((uint32_t)(k >> 32)); }
+
+// Stage 2a: the filter against the winner over all shards has flagged this
+// shard's rays with kept queue entries; a ray whose own FP32 winner is not
+// that winner but lies within its tie band is flagged as well.  Exported as
+// one byte per ray for the MAX exchange.
+__global__ void k_shard_flags(CastArgs a) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_rays_total; g += stride) {
+        const unsigned long long kl = a.keys[g], kg = a.keys_glob[g];
+        bool f = (a.flag_bits[g >> 5] >> (g & 31u)) & 1u;
+        if (!f && (uint32_t)kl != NO_HIT && rebase_key(kl, a.tri_base) != kg &&
+            key_t(kl) <= __fmul_rn(key_t(kg), 1.f + BETA))
+            f = true;
+        a.flags_out[g] = f ? 1 : 0;
+    }
+}
+
+// Stage 2b: a ray some shard flagged is re-tested here too when this shard's
+// FP32 winner lies within the tie band of the winner over all shards (the
+// shard that holds that winner included), so that the final MIN compares FP64
+// results only.
+__global__ void k_shard_join(CastArgs a) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_rays_total; g += stride) {
+        if (!a.flags_any[g]) continue;
+        const unsigned long long kl = a.keys[g];
+        if ((uint32_t)kl == NO_HIT || (a.flag_bits[g >> 5] >> (g & 31u)) & 1u) continue;
+        if (key_t(kl) <= __fmul_rn(key_t(a.keys_glob[g]), 1.f + BETA)) flag_ray(a, g);
+    }
+}
+
+// the shard's keys with global triangle ids (base + local id); resolved: the
+// FP64 key for flagged rays
+__global__ void k_shard_export(CastArgs a, uint32_t base, int resolved) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < a.n_rays_total; g += stride) {
+        unsigned long long k = a.keys[g];
+        if (resolved && (a.flag_bits[g >> 5] >> (g & 31u) & 1u)) k = a.keys64[g];
+        a.keys_out[g] = rebase_key(k, base);
+    }
 }
 
 // output function of SplitMix64 (Steele, Lea and Flood, 2014) for state x
@@ -2681,6 +2740,12 @@ static void launch_cull_split(const CastArgs& a, const CastArgs& ac, bool do_a, 
     }
 }
 
+// key -> (distance, id) of finished keys (the last stage of a sharded cast)
+void launch_decode(const CastArgs& a, int n_sm, cudaStream_t st) {
+    const int nb = (int)std::min<uint32_t>((a.n_rays_total + 255) / 256, (uint32_t)n_sm * 8);
+    k_decode<<<std::max(nb, 1), 256, 0, st>>>(a, 0);
+}
+
 int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t st, const KernelMarks* marks,
                  FrameSplit split) {
     const bool recheck = a.flags & 1u;
@@ -2689,6 +2754,32 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
     std::function<void(int, int)> mark = [&](int k, int phase) {
         if (marks && marks->fn) marks->fn(marks->user, k, phase, st);
     };
+    const int nb = (int)std::min<uint32_t>((a.n_rays_total + 255) / 256, (uint32_t)n_sm * 8);
+    if (split.stage == 2) {
+        // the filter against the winner over all shards, then the exported flags
+        if (recheck) {
+            mark(K_RECHECK_FILTER, 0);
+            k_recheck_filter<<<n_sm * 2, 256, 0, st>>>(a);
+            mark(K_RECHECK_FILTER, 1);
+        }
+        k_shard_flags<<<std::max(nb, 1), 256, 0, st>>>(a);
+        return launches + (recheck ? 2 : 1);
+    }
+    if (split.stage == 3) {
+        // the rays flagged by any shard, the FP64 re-tests, the resolved keys
+        if (recheck) {
+            k_shard_join<<<std::max(nb, 1), 256, 0, st>>>(a);
+            mark(K_RECHECK_RAYS, 0);
+            k_recheck_rays<<<n_sm * 2, 256, 0, st>>>(a);
+            mark(K_RECHECK_RAYS, 1);
+            mark(K_RECHECK_PAIRS, 0);
+            k_recheck_pairs<<<n_sm * 2, RECHECK_BLOCK, 0, st>>>(a);
+            mark(K_RECHECK_PAIRS, 1);
+            launches += 3;
+        }
+        k_shard_export<<<std::max(nb, 1), 256, 0, st>>>(a, a.tri_base, recheck ? 1 : 0);
+        return launches + 1;
+    }
     // the triangle range of this part's elevation cull
     CastArgs ac = a;
     if (split.part == 1) ac.n_tris = std::max(std::min(split.at, a.n_tris), a.tri_first);
@@ -2743,6 +2834,14 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
         mark(K_REFINE, 0);
         k_refine<<<n_sm * 2, 256, 0, st>>>(a);
         mark(K_REFINE, 1);
+        launches++;
+    }
+    if (split.stage == 1) {
+        // FP32 pass of a sharded cast: export the keys
+        k_shard_export<<<std::max(nb, 1), 256, 0, st>>>(a, a.tri_base, 0);
+        return launches + 1;
+    }
+    if (recheck) {
         mark(K_RECHECK_FILTER, 0);
         k_recheck_filter<<<n_sm * 2, 256, 0, st>>>(a);
         mark(K_RECHECK_FILTER, 1);
@@ -2752,9 +2851,9 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
         mark(K_RECHECK_PAIRS, 0);
         k_recheck_pairs<<<n_sm * 2, RECHECK_BLOCK, 0, st>>>(a);
         mark(K_RECHECK_PAIRS, 1);
-        launches += 4;
+        launches += 3;
     }
-    int dec_blocks = (int)std::min<uint32_t>((a.n_rays_total + 255) / 256, (uint32_t)n_sm * 8);
+    int dec_blocks = nb;
     mark(K_DECODE, 0);
     k_decode<<<max(dec_blocks, 1), 256, 0, st>>>(a, recheck ? 1 : 0);
     mark(K_DECODE, 1);

@@ -70,7 +70,7 @@ EXPORTS = ["grca_create", "grca_destroy", "grca_create_sensor", "grca_set_sensor
            "grca_get_stats", "grca_last_launch_count", "grca_profile_enable", "grca_profile_read",
            "grca_status_string", "grca_last_cuda_error", "grca_cast_noalloc",
            "grca_set_ray_mask", "grca_set_sensor_azimuths", "grca_set_range_noise", "grca_build_static",
-           "grca_get_launch_config", "grca_host_wait"]
+           "grca_get_launch_config", "grca_host_wait", "grca_cast_shard", "grca_flag_shard", "grca_resolve_shard", "grca_decode_keys"]
 
 
 def library_path() -> str:
@@ -104,6 +104,14 @@ def _lib_handle(build_if_missing: bool = True):
     lib.grca_cast.restype = i32
     lib.grca_cast_host.argtypes = [P, P, u32, P, u32, u32, P, P, u32, P]
     lib.grca_cast_host.restype = i32
+    lib.grca_cast_shard.argtypes = [P, P, u32, u32, P, u32, P]
+    lib.grca_cast_shard.restype = i32
+    lib.grca_flag_shard.argtypes = [P, P, P, P]
+    lib.grca_flag_shard.restype = i32
+    lib.grca_resolve_shard.argtypes = [P, P, P, P]
+    lib.grca_resolve_shard.restype = i32
+    lib.grca_decode_keys.argtypes = [P, P, P, P, P]
+    lib.grca_decode_keys.restype = i32
     lib.grca_host_wait.argtypes = [P, u32]
     lib.grca_host_wait.restype = i32
     lib.grca_autotune.argtypes = [P, P, u32, P, P, u32, P, ctypes.POINTER(ctypes.c_float)]
@@ -329,6 +337,31 @@ class Caster:
         st = self.lib.grca_cast(self.ctx, ids_a.ctypes.data, ids_a.shape[0], dist.data_ptr(), tri.data_ptr(),
                                 int(flags), _stream_ptr(stream))
         self._check(st, "grca_cast")
+        return dist, tri
+
+    # triangle-sharded casts (include/grca.h): key arrays are int64 tensors on
+    # this context's device, one entry per ray
+    def cast_shard(self, ids: Sequence[int], tri_base: int, keys, flags: int = 0, stream=None):
+        ids_a = np.ascontiguousarray(ids, dtype=np.int32)
+        st = self.lib.grca_cast_shard(self.ctx, ids_a.ctypes.data, ids_a.shape[0], int(tri_base), keys.data_ptr(),
+                                      int(flags), _stream_ptr(stream))
+        self._check(st, "grca_cast_shard")
+        return keys
+
+    def flag_shard(self, keys_min, flags_out, stream=None):
+        st = self.lib.grca_flag_shard(self.ctx, keys_min.data_ptr(), flags_out.data_ptr(), _stream_ptr(stream))
+        self._check(st, "grca_flag_shard")
+        return flags_out
+
+    def resolve_shard(self, flags_any, keys_out, stream=None):
+        st = self.lib.grca_resolve_shard(self.ctx, flags_any.data_ptr(), keys_out.data_ptr(), _stream_ptr(stream))
+        self._check(st, "grca_resolve_shard")
+        return keys_out
+
+    def decode_keys(self, keys, out, stream=None):
+        dist, tri = out
+        st = self.lib.grca_decode_keys(self.ctx, keys.data_ptr(), dist.data_ptr(), tri.data_ptr(), _stream_ptr(stream))
+        self._check(st, "grca_decode_keys")
         return dist, tri
 
     def cast_host(self, ids, dyn_tris: Optional[np.ndarray], first_dyn: int, out_dist: np.ndarray,
