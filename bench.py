@@ -42,7 +42,11 @@ F_SETUP = 200.0   # FP32 flops per live pair: the test setup (edge normals, erro
 F_TEST = 30.0     # FP32 flops per candidate ray-triangle test
 F_CULL = 200.0    # whole-frame unit: FP32 flops per (triangle, sensor) pair of the culls (150-250)
 TRI_BYTES = 36.0
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_2605_10457_gb300", "csrc", f) for f in ("grca_kernels.cu", "grca_internal.h")]
+# the code a committed DRAM capture depends on: the kernels, the launch
+# parameters chosen by the runtime, and the compiler flags
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2605_10457_gb300", "csrc", f)
+                  for f in ("grca_kernels.cu", "grca_internal.h", "grca_api.cu")] + \
+                 [os.path.join(ROOT, "paper_2605_10457_gb300", "build.py")]
 
 
 def kernels_digest(sources=None) -> str:
@@ -54,8 +58,11 @@ def kernels_digest(sources=None) -> str:
     h = hashlib.sha256()
     for f in sources or KERNEL_SOURCES:
         src = open(f).read()
-        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
-        src = re.sub(r"//[^\n]*", " ", src)
+        if f.endswith(".py"):
+            src = re.sub(r"#[^\n]*", " ", src)
+        else:
+            src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+            src = re.sub(r"//[^\n]*", " ", src)
         h.update(" ".join(src.split()).encode())
     return h.hexdigest()
 
@@ -388,7 +395,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c5")
     ap.add_argument("--frames", type=int, default=8, help="distinct animated frames kept on the device")
+    ap.add_argument("--subset", type=int, default=0,
+                    help="profiling captures: only the first N triangles of the workload's frame 0, no animation "
+                         "(with --lean; inputs still larger than L2 for N above ~4 M)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--launch-config", default=None,
+                    help="inline_max,chunk_rays,cull_block,cull_blocks_per_sm: use this launch configuration instead "
+                         "of the autotuner's (profiler captures of the benchmark's own configuration)")
     ap.add_argument("--cpu-budget", type=float, default=12.0,
                     help="seconds of single-core oracle work for the single-core rate; 0 skips the oracle legs")
     ap.add_argument("--acc-rays", type=int, default=48, help="graded stratified rays per sensor (accuracy leg)")
@@ -439,12 +452,22 @@ def main():
     ns, nd = sc.n_static, sc.n_dynamic
     frames_host = [sc.dynamic_tris(f % sc.n_frames) for f in range(args.frames)]
     full0 = np.ascontiguousarray(np.concatenate([sc.static_tris, frames_host[0]], 0))
+    if args.subset:
+        # a static prefix of the scene for profiler captures
+        full0 = np.ascontiguousarray(full0[:args.subset])
+        ns, nd = full0.shape[0], 0
+        frames_host = [full0[:0]]
+        args.lean = True
     frames_dev = torch.from_numpy(np.stack(frames_host, 0)).to(dev)       # [F, nd, 3, 3]
 
     caps = dict(big_pair_capacity=48 << 20, chunk_capacity=512 << 20, recheck_capacity=64 << 20)
     if args.capacity == "small":
         caps = dict(big_pair_capacity=8 << 20, chunk_capacity=48 << 20, recheck_capacity=16 << 20,
                     survivor_capacity=96 << 20)
+    if args.launch_config:
+        lc = [int(x) for x in args.launch_config.split(",")]
+        caps.update(inline_max=lc[0], chunk_rays=lc[1], cull_block=lc[2], cull_blocks_per_sm=lc[3])
+        args.no_autotune = True
     c = grca.Caster(local, **caps)
     ids = [c.add_sensor(s) for s in sc.sensors]
     c.upload(full0)
@@ -466,7 +489,8 @@ def main():
 
     def step_batched(k):
         f = frame_of(rank, ws, k, args.frames)
-        c.update(frames_dev[f], ns)
+        if nd:
+            c.update(frames_dev[f % frames_dev.shape[0]], ns)
         c.cast(ids, FL | grca.CAST_GRAPH, out)
 
     # plain path: one sensor per cast, FP32 only, each into its slice of the outputs

@@ -26,7 +26,9 @@ constexpr int MAX_CHANNELS = 1024;
 constexpr int MAX_RAYS = 32768;
 
 // queue counters (device uint32[8])
-enum { Q_BIG = 0, Q_CHUNK = 1, Q_RECHECK = 2, Q_FLAG = 3, Q_DUMP = 4, Q_SURV = 5, Q_SURV_SPLIT = 6, Q_NUM = 8 };
+// Q_REFINE_N: the re-test queue's length before k_refine, which appends to it
+enum { Q_BIG = 0, Q_CHUNK = 1, Q_RECHECK = 2, Q_FLAG = 3, Q_DUMP = 4, Q_SURV = 5, Q_SURV_SPLIT = 6, Q_REFINE_N = 7,
+       Q_NUM = 8 };
 // statistics counters (device u64[C_NUM])
 enum {
     C_PAIRS = 0, C_PAIRS_LIVE, C_CAND, C_CAND_INLINE, C_BIG, C_CHUNKS, C_TESTS, C_HITS,

@@ -2229,8 +2229,12 @@ __device__ __forceinline__ void decode_ray(const CastArgs& a, uint32_t g, uint32
     i = loc - j * S.n_rays;
 }
 
-// returns the u64 key of the FP64 result (KEY_MISS on a miss)
-__device__ unsigned long long test_fp64(const CastArgs& a, uint32_t g, uint32_t tri) {
+// returns the u64 key of the FP64 result (KEY_MISS on a miss).  edges =
+// false skips the edge functions: for a (ray, triangle) pair that the FP32
+// test found inside every edge with margin (a certain hit, or an entry
+// uncertain only in t or in the range), whose FP64 edge functions are
+// positive too; every other step is the same, so the key is the same bits.
+__device__ unsigned long long test_fp64(const CastArgs& a, uint32_t g, uint32_t tri, bool edges = true) {
     uint32_t sn, j, i;
     decode_ray(a, g, sn, j, i);
     const SensorDev& S = a.sensors[sn];
@@ -2255,7 +2259,7 @@ __device__ unsigned long long test_fp64(const CastArgs& a, uint32_t g, uint32_t 
     // canonical edge functions (same rule as the FP32 test): base = the
     // lexicographically smaller vertex, evaluated from it; selects, no arrays
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 3 && edges; ++k) {
         const V3 fa = k == 0 ? f0 : (k == 1 ? f1 : f2), fb = k == 0 ? f1 : (k == 1 ? f2 : f0);
         const D3 va = k == 0 ? v0 : (k == 1 ? v1 : v2), vb = k == 0 ? v1 : (k == 1 ? v2 : v0);
         const D3 wa = k == 0 ? w0 : (k == 1 ? w1 : w2), wb = k == 0 ? w1 : (k == 1 ? w2 : w0);
@@ -2280,8 +2284,13 @@ __device__ unsigned long long test_fp64(const CastArgs& a, uint32_t g, uint32_t 
 // uncertain stays for the FP64 re-test.  Runs after every FP32 test of the
 // frame, before the filter, so the commit order does not matter: the tie
 // chain of the FP32 commits holds for any order.
+// the queue length k_refine works on, taken by the launch before it: k_refine
+// appends tie entries to the same queue, and a block that started late would
+// otherwise count slots reserved by other blocks but not written yet
+__global__ void k_refine_count(CastArgs a) { a.qcount[Q_REFINE_N] = *(volatile uint32_t*)&a.qcount[Q_RECHECK]; }
+
 __global__ void k_refine(CastArgs a) {
-    const uint32_t np = min(*(volatile uint32_t*)&a.qcount[Q_RECHECK], a.recheck_cap);
+    const uint32_t np = min(a.qcount[Q_REFINE_N], a.recheck_cap);
     uint32_t n_ref = 0, n_hit = 0, n_ties = 0;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < np; q += gridDim.x * blockDim.x) {
         const uint4 e = a.recheck[q];
@@ -2360,7 +2369,8 @@ __global__ void k_recheck_rays(CastArgs a) {
         uint32_t g = a.flag_list[q];
         unsigned long long k = a.keys[g];
         uint32_t id = (uint32_t)k;
-        a.keys64[g] = id == NO_HIT ? KEY_MISS : test_fp64(a, g, id);
+        // the FP32 winner is a certain hit: inside every edge with margin
+        a.keys64[g] = id == NO_HIT ? KEY_MISS : test_fp64(a, g, id, false);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_FLAGGED] = *(volatile uint32_t*)&a.qcount[Q_FLAG];
 }
@@ -2371,9 +2381,12 @@ constexpr int RECHECK_BLOCK = 256;
 // at a small fraction of the FP32 rate, and a warp pays for a test however
 // few of its lanes take part, so each warp first compacts the kept pairs of
 // its slices of the queue into shared memory and tests them 32 at a time.
+// pr.x: ray | bit 31 set when the entry needs the FP64 edge functions (cause
+// edge or orientation; ray ids stay below 2^31: 64 sensors x 1024 x 32768)
 __device__ __forceinline__ void recheck_pair(const CastArgs& a, uint2 pr) {
-    const unsigned long long k = test_fp64(a, pr.x, pr.y);
-    if (k != KEY_MISS) atomicMin(&a.keys64[pr.x], k);
+    const uint32_t g = pr.x & 0x7FFFFFFFu;
+    const unsigned long long k = test_fp64(a, g, pr.y, (pr.x >> 31) != 0u);
+    if (k != KEY_MISS) atomicMin(&a.keys64[g], k);
 }
 __global__ void __launch_bounds__(RECHECK_BLOCK) k_recheck_pairs(CastArgs a) {
     __shared__ uint2 buf[RECHECK_BLOCK / 32][64];
@@ -2387,7 +2400,8 @@ __global__ void __launch_bounds__(RECHECK_BLOCK) k_recheck_pairs(CastArgs a) {
         uint2 pr = make_uint2(0u, NO_HIT);
         if (q < np) {
             const uint4 e = a.recheck[q];
-            pr = make_uint2(e.x, e.y);
+            const bool edges = e.w == (uint32_t)UC_EDGE || e.w == (uint32_t)UC_ORIENT;
+            pr = make_uint2(e.x | (edges ? 0x80000000u : 0u), e.y);
         }
         const bool keep = pr.y != NO_HIT;
         const uint32_t bal = __ballot_sync(0xffffffffu, keep);
@@ -2770,10 +2784,10 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
         if (recheck) {
             k_shard_join<<<std::max(nb, 1), 256, 0, st>>>(a);
             mark(K_RECHECK_RAYS, 0);
-            k_recheck_rays<<<n_sm * 2, 256, 0, st>>>(a);
+            k_recheck_rays<<<n_sm * 8, 256, 0, st>>>(a);
             mark(K_RECHECK_RAYS, 1);
             mark(K_RECHECK_PAIRS, 0);
-            k_recheck_pairs<<<n_sm * 2, RECHECK_BLOCK, 0, st>>>(a);
+            k_recheck_pairs<<<n_sm * 4, RECHECK_BLOCK, 0, st>>>(a);
             mark(K_RECHECK_PAIRS, 1);
             launches += 3;
         }
@@ -2832,9 +2846,10 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
     }
     if (recheck) {
         mark(K_REFINE, 0);
-        k_refine<<<n_sm * 2, 256, 0, st>>>(a);
+        k_refine_count<<<1, 1, 0, st>>>(a);
+        k_refine<<<n_sm * 8, 256, 0, st>>>(a);
         mark(K_REFINE, 1);
-        launches++;
+        launches += 2;
     }
     if (split.stage == 1) {
         // FP32 pass of a sharded cast: export the keys
@@ -2846,10 +2861,10 @@ int launch_frame(const CastArgs& a, const LaunchCfg& cfg, int n_sm, cudaStream_t
         k_recheck_filter<<<n_sm * 2, 256, 0, st>>>(a);
         mark(K_RECHECK_FILTER, 1);
         mark(K_RECHECK_RAYS, 0);
-        k_recheck_rays<<<n_sm * 2, 256, 0, st>>>(a);
+        k_recheck_rays<<<n_sm * 8, 256, 0, st>>>(a);
         mark(K_RECHECK_RAYS, 1);
         mark(K_RECHECK_PAIRS, 0);
-        k_recheck_pairs<<<n_sm * 2, RECHECK_BLOCK, 0, st>>>(a);
+        k_recheck_pairs<<<n_sm * 4, RECHECK_BLOCK, 0, st>>>(a);
         mark(K_RECHECK_PAIRS, 1);
         launches += 3;
     }

@@ -214,14 +214,17 @@ def test_grazing_hits_get_exact_distances_without_the_fp64_queue():
     assert rel.max() <= 1e-6, rel.max()
 
 
-def test_candidate_spans_cover_every_exact_hit():
+@pytest.mark.parametrize("cfg", ["c1", "c2m", "c3m", "c4m", "c5m"])
+def test_candidate_spans_cover_every_exact_hit(cfg):
     """Every (ray, triangle) pair that the FP64 oracle finds hitting must be
-    among the candidates the culling passes emit (debug dump)."""
+    among the candidates the culling passes emit (debug dump), for every
+    sensor of the scene: the culls never drop a true hit, whatever the test
+    then decides."""
     import torch
     from paper_2605_10457_gb300.grca import CAST_DUMP_CANDIDATES
-    sc = scene_c1()
-    c, ids, tris = _setup(sc)
-    cap = 8_000_000
+    sc = scene_c1() if cfg == "c1" else make_config(cfg)
+    c, ids, tris = _setup(sc, frame=0 if cfg == "c1" else 2)
+    cap = 24_000_000
     pairs = torch.zeros(2 * cap, dtype=torch.int32, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
     c.set_debug_dump(pairs, cnt)
@@ -229,11 +232,16 @@ def test_candidate_spans_cover_every_exact_hit():
     n = int(cnt.item())
     assert 0 < n <= cap
     got = pairs[:2 * n].view(-1, 2).cpu().numpy().astype(np.int64)
-    cand = set((got[:, 1] << 32 | got[:, 0]).tolist())
-    hits = oracle.triangle_hits(sc.sensors[0], tris)
-    need = (hits[:, 0] << 32) | hits[:, 1]
-    missing = [int(x) for x in need if int(x) not in cand]
-    assert not missing, missing[:10]
+    cand = np.unique((got[:, 1] << 32) | got[:, 0])
+    off = 0
+    # every sensor on the small scenes; the first two (of eight) on c4m / c5m,
+    # whose all-pairs oracle pass takes about 10 s per sensor
+    for s in sc.sensors[:2] if cfg in ("c4m", "c5m") else sc.sensors:
+        hits = oracle.triangle_hits(s, tris)   # (triangle, local ray id)
+        need = (hits[:, 0] << 32) | (hits[:, 1] + off)
+        missing = need[~np.isin(need, cand)]
+        assert missing.size == 0, (cfg, off, missing[:10])
+        off += s.n_channels * s.n_rays
     c.set_debug_dump(None)
 
 
