@@ -717,6 +717,7 @@ static void fill_sensor(const grca_ctx* ctx, int id, uint32_t ray_off, SensorDev
     s.d_min = (float)d.d_min;
     s.d_max = std::isfinite(d.d_max) ? (float)d.d_max : INFINITY;
     s.period = (float)(2 * M_PI / d.dtheta);
+    s.inv_period = 1.0f / (h.full ? (float)d.n_rays : s.period);
     s.n_ch = d.n_channels;
     s.n_rays = d.n_rays;
     s.ch_off = ctx->ch_off[id];

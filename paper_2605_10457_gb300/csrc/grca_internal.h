@@ -58,7 +58,7 @@ struct SensorDev {
     float o_hi[3], o_lo[3];  // origin = o_hi + o_lo (float pair)
     float B[9];           // rows f, r, u (FP32)
     float B_lo[9];        // B64 - B (FP32): the double-float rotation of the t refinement
-    float pad3_;
+    float inv_period;     // 1 / (full ? n_rays : period), correctly rounded
     float theta0, dtheta, inv_dtheta;
     float d_min, d_max;
     float period;         // 2*pi/dtheta, in rays

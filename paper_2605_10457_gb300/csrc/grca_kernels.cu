@@ -140,8 +140,33 @@ struct SetupWriterSoA {
     __device__ __forceinline__ void set(int k, float v) { base[k * 32 + i] = v; }
 };
 
+// Hardware approximations in their flush-to-zero forms: the plain forms add
+// a rescaling of subnormal inputs and results to every call, which the
+// culls pay per pair.  Each call site below stays conservative when a
+// subnormal input is taken as zero: rsqrt and rcp then return +inf (a bound
+// opens fully), sqrt returns 0 where the bounds' absolute padding covers the
+// lost 1e-19, and the operand of rcp_up is clamped into the range where its
+// result stays normal, on the side that makes the bound larger.  A NaN input
+// stays NaN.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_ftz(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float div_ftz(float a, float b) {
+    float r;
+    asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
 // upper bounds for error-bound arithmetic: hardware approximations (relative
-// error <= 2^-22) scaled up by 1 + 2^-18.9
+// error <= 2^-22) scaled up by 1 + 2^-18.9; rcp_up of at most 2^126 (so that
+// the result stays normal).  sqrt_up keeps the plain form (its flush-to-zero
+// form costs k_cull_b a register spill)
 __device__ __forceinline__ float sqrt_up(float x) {
     float r;
     asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -149,7 +174,8 @@ __device__ __forceinline__ float sqrt_up(float x) {
 }
 __device__ __forceinline__ float rcp_up(float x) {
     float r;
-    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    const float xc = x > 8.50705917e37f ? 8.50705917e37f : x;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(xc));
     return __fmul_rn(r, 1.000002f);
 }
 
@@ -549,7 +575,7 @@ __device__ __forceinline__ float ray_units(const SensorDev& S, float theta) {
     // normalise into one period [g0, g0 + P); P = n_rays for full circles
     float P = S.full ? (float)S.n_rays : S.period;
     float g0 = S.full ? 0.f : -0.5f * (S.period - (float)S.n_rays);
-    x -= P * floorf((x - g0) * __frcp_rn(P));
+    x -= P * floorf((x - g0) * S.inv_period);
     return x;
 }
 
@@ -609,7 +635,7 @@ __device__ __forceinline__ float rel_angle(V3 a, V3 b) {
     float cr = cross2(a, b), dt = dot2(a, b);
     if (dt > 0.f && fabsf(cr) < 0.02f * dt) {
         // |x| < 0.02; the fast division's 2-ulp error adds < 1e-8 rad
-        float x = __fdividef(cr, dt), x2 = x * x;
+        float x = div_ftz(cr, dt), x2 = x * x;
         return x * (1.f - x2 * (0.33333334f - 0.2f * x2));
     }
     return fast_atan2(cr, dt);  // callers pad by FAST_ATAN_PAD per call
@@ -646,7 +672,7 @@ constexpr float FAST_ATAN_PAD = 2e-6f;
 __device__ __forceinline__ float fast_atan2(float y, float x) {
     float ax = fabsf(x), ay = fabsf(y);
     float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-    float t = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+    float t = mx > 0.f ? div_ftz(mn, mx) : 0.f;
     float t2 = t * t;
     float r = fmaf(t2, ATAN_C6, ATAN_C5);
     r = fmaf(t2, r, ATAN_C4);
@@ -805,11 +831,12 @@ __device__ __forceinline__ bool elev_range_w(const SensorDev& S, const V3 w[3], 
     return pierced;
 }
 
-// azimuth padding of vertex p from |p|^2 and |p_h|^2
+// azimuth padding of vertex p from |p|^2 and |p_h|^2 (10 rad, the full
+// circle, near the vertical axis and where r2 * h2 could overflow)
 __device__ __forceinline__ float az_pad2(V3 p) {
     float h2 = p.x * p.x + p.y * p.y;
     float r2 = h2 + p.z * p.z;
-    return h2 > 1e-12f * r2 ? 16.f * U32 * r2 * rsqrtf(r2 * h2) : 10.f;
+    return h2 > 1e-12f * r2 && r2 < 1e18f ? 16.f * U32 * r2 * rsqrt_ftz(r2 * h2) : 10.f;
 }
 
 // closest-point distance from the origin to the triangle (w = vertices
@@ -1500,18 +1527,19 @@ __device__ __forceinline__ bool cull_elev(const ElevSensor& E, const SensorDev& 
     if (E.dmax < INFINITY) {
         // range pre-cull (App. A.4.1 Step 1), only where provably empty: every
         // point of the triangle lies within lmax (the longest edge) of vertex 0
-        const float d0 = sqrtf(r2[0]);
+        // (the approximate root's 2^-22 relative error is inside the bounds' padding)
+        const float d0 = sqrt_ftz(r2[0]);
         if (d0 - lmax > E.dmax || d0 + lmax < E.dmin) return false;
     }
     if ((flags & 32u) && !elev_area_keep(S, v[0], v[1], v[2], area_eps2)) return false;
     // a vertex at the origin gives 0 * inf = NaN, which fminf / fmaxf skip;
     // r2min = 0 then makes dev huge below, so the range opens fully
-    const float sv0 = z[0] * rsqrtf(r2[0]), sv1 = z[1] * rsqrtf(r2[1]), sv2 = z[2] * rsqrtf(r2[2]);
+    const float sv0 = z[0] * rsqrt_ftz(r2[0]), sv1 = z[1] * rsqrt_ftz(r2[1]), sv2 = z[2] * rsqrt_ftz(r2[2]);
     const float smin = fminf(sv0, fminf(sv1, sv2)), smax = fmaxf(sv0, fmaxf(sv1, sv2));
     const float r2min = fminf(r2[0], fminf(r2[1], r2[2]));
     const float r2max = fmaxf(r2[0], fmaxf(r2[1], r2[2]));
     const float h2min = fminf(h2[0], fminf(h2[1], h2[2]));
-    const float rinv = rsqrtf(fmaxf(r2min, 1e-37f));
+    const float rinv = rsqrt_ftz(fmaxf(r2min, 1e-37f));
     // |w[k1]-w[k]|^2 <= 1.0001 |E|^2 + 5.7e-10 |w|^2 for the FP32 rounding of w
     const float ee_p = fmaf(5.7e-10f, r2max, 1.0001f * ee_max);
     const float dev = fmaf(0.3100004f * ee_p, rinv * rinv, fmaf(E.olo, rinv, EPS_S));
@@ -1606,7 +1634,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
         if (nw.x == 0.f && nw.y == 0.f && nw.z == 0.f) valid = false;  // zero area: never hit
         // longest edge (squared; and rounded-up length), sensor independent
         const float ee_max = fmaxf(vdot(e0, e0), fmaxf(vdot(e1, e1), vdot(e2, e2)));
-        const float lmax = sqrtf(ee_max) * (1.f + 1e-6f);
+        const float lmax = sqrt_ftz(ee_max) * (1.f + 1e-6f);
 #pragma unroll 1
         for (uint32_t k = 0; k < ns; ++k) {
             if (!((live >> k) & 1u)) continue;  // warp-uniform
@@ -3014,6 +3042,7 @@ extern "C" grca_status grca_cast_noalloc(const grca_sensor_desc* d, const float*
     s.n_rays = d->n_rays;
     s.full = std::fabs(d->n_rays * d->dtheta - 2 * M_PI) <= 1e-9 ? 1u : 0u;
     s.has_range = (d->d_min > 0.0 || std::isfinite(d->d_max)) ? 1u : 0u;
+    s.inv_period = 1.0f / (s.full ? (float)s.n_rays : s.period);
     double det = d->f[0] * (d->r[1] * d->u[2] - d->r[2] * d->u[1]) - d->f[1] * (d->r[0] * d->u[2] - d->r[2] * d->u[0]) +
                  d->f[2] * (d->r[0] * d->u[1] - d->r[1] * d->u[0]);
     s.hand = det < 0.0 ? -1.f : 1.f;
