@@ -84,9 +84,15 @@ __device__ __forceinline__ bool lex_less(V3 a, V3 b) {
 }
 __device__ __forceinline__ float cross2(V3 a, V3 b) { return a.x * b.y - a.y * b.x; }
 __device__ __forceinline__ float dot2(V3 a, V3 b) { return a.x * b.x + a.y * b.y; }
+// a mod n in [0, n) for n > 0: one period either way without a division
+// (the usual case), the division only beyond
 __device__ __forceinline__ int imod(int a, int n) {
-    int r = a % n;
-    return r < 0 ? r + n : r;
+    int r = a < 0 ? a + n : (a >= n ? a - n : a);
+    if ((unsigned)r >= (unsigned)n) {
+        r = a % n;
+        if (r < 0) r += n;
+    }
+    return r;
 }
 
 // ---------------------------------------------------------------------------
