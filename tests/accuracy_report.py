@@ -188,7 +188,7 @@ def write_md(rows, md_path, inp):
         tot["rays"] += r["rays"]
         fl = a["stats"]["flagged_rays"]
         nr = a["stats"]["n_rays"]
-        L.append(f"| {r['workload']} | {r['rays']:,}" + (f" ({r['stress_rays']} stress)" if r["stress_rays"] else "") +
+        L.append(f"| {r['workload'].replace('|', ', ')} | {r['rays']:,}" + (f" ({r['stress_rays']} stress)" if r["stress_rays"] else "") +
                  f" | {a['oracle_hits']:,} | {a['errors']} ({a['id_mismatch']} / {a['hit_miss']} / {a['dist_bad']}) | "
                  f"{a['tie_accepted']} / {a['edge_accepted']} | {a['max_rel_dist_err']:.2e} / "
                  f"{a['median_rel_dist_err']:.1e} | {b['errors']} ({b['id_mismatch']} / {b['hit_miss']} / "
