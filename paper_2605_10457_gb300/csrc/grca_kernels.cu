@@ -639,7 +639,7 @@ __device__ __forceinline__ float fast_atan2(float y, float x);
 // larger ones by fast_atan2 (error < FAST_ATAN_PAD)
 __device__ __forceinline__ float rel_angle(V3 a, V3 b) {
     float cr = cross2(a, b), dt = dot2(a, b);
-    if (dt > 0.f && fabsf(cr) < 0.02f * dt) {
+    if (dt >= 1.17549435e-38f && fabsf(cr) < 0.02f * dt) {
         // |x| < 0.02; the fast division's 2-ulp error adds < 1e-8 rad
         float x = div_ftz(cr, dt), x2 = x * x;
         return x * (1.f - x2 * (0.33333334f - 0.2f * x2));
@@ -678,7 +678,8 @@ constexpr float FAST_ATAN_PAD = 2e-6f;
 __device__ __forceinline__ float fast_atan2(float y, float x) {
     float ax = fabsf(x), ay = fabsf(y);
     float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-    float t = mx > 0.f ? div_ftz(mn, mx) : 0.f;
+    // (a subnormal mx would be flushed to zero by the division)
+    float t = mx >= 1.17549435e-38f ? div_ftz(mn, mx) : 0.f;
     float t2 = t * t;
     float r = fmaf(t2, ATAN_C6, ATAN_C5);
     r = fmaf(t2, r, ATAN_C4);
@@ -1538,8 +1539,8 @@ __device__ __forceinline__ bool cull_elev(const ElevSensor& E, const SensorDev& 
         if (d0 - lmax > E.dmax || d0 + lmax < E.dmin) return false;
     }
     if ((flags & 32u) && !elev_area_keep(S, v[0], v[1], v[2], area_eps2)) return false;
-    // a vertex at the origin gives 0 * inf = NaN, which fminf / fmaxf skip;
-    // r2min = 0 then makes dev huge below, so the range opens fully
+    // a vertex at (or within 1e-8 of) the origin can give inf or 0 * inf =
+    // NaN here; such a triangle takes the full range below (r2min < 1e-16)
     const float sv0 = z[0] * rsqrt_ftz(r2[0]), sv1 = z[1] * rsqrt_ftz(r2[1]), sv2 = z[2] * rsqrt_ftz(r2[2]);
     const float smin = fminf(sv0, fminf(sv1, sv2)), smax = fmaxf(sv0, fmaxf(sv1, sv2));
     const float r2min = fminf(r2[0], fminf(r2[1], r2[2]));
@@ -1553,12 +1554,17 @@ __device__ __forceinline__ bool cull_elev(const ElevSensor& E, const SensorDev& 
     // never tested; a non-finite vertex takes the overflow branch below)
     float lo = smin - dev, hi = smax + dev;
     bool pierced = false;
-    // the vertical axis can meet the projected triangle only if its nearest
+    // The vertical axis can meet the projected triangle only if its nearest
     // vertex lies within the longest edge of the axis (with margins for the
-    // FP32 rounding and for o_lo: (h + d)^2 <= 1.01 h^2 + 101 d^2)
-    if (h2min <= fmaf(8.2f * U32, r2max, fmaf(1.0201f, ee_max, E.thr0)) || !(r2max < 3e38f)) {
-        if (!(r2max < 3e38f)) {
-            // a vertex so far away that |w|^2 overflows: every channel, full circle
+    // FP32 rounding and for o_lo: (h + d)^2 <= 1.01 h^2 + 101 d^2).  A vertex
+    // so far away that |w|^2 overflows, or within 1e-8 of the origin (it
+    // enters the branch since h2min <= r2min), opens every channel and the
+    // full circle: near the origin |w|^2 may be subnormal (the flush-to-zero
+    // root above then returns +inf), and the per-channel crossings of a
+    // deferred pair (k_expand) take products of four coordinates, which
+    // underflow below about 1e-9.5.
+    if (!(h2min > fmaxf(fmaf(8.2f * U32, r2max, fmaf(1.0201f, ee_max, E.thr0)), 1e-16f)) || !(r2max < 3e38f)) {
+        if (!(r2max < 3e38f) || !(r2min >= 1e-16f)) {
             lo = -2.f;
             hi = 2.f;
             pierced = true;

@@ -128,6 +128,46 @@ def test_tiny_random_scenes_brute_equals_culled():
         assert g["errors"] == 0, (seed, g)
 
 
+def test_geometry_at_the_sensor_origin_brute_equals_culled():
+    """Triangles at a sensor's origin: a vertex exactly at it (its plane
+    passes through the origin: no hit from there), triangles 1e-7 .. 1e-5
+    and 1e-16 .. 1e-12 across around it, and microscopic ones 1e-20 across,
+    whose |w|^2 and the products of the FP32 bounds are subnormal or zero.
+    No hit is lost: culled == brute in both modes, and the FP32 + FP64
+    re-test cast grades with zero errors against the oracle (the FP64 re-test
+    settles the pairs whose FP32 test underflows).  Each triangle spans a
+    small range of magnitudes, so the FP64 oracle stays exact on it."""
+    from paper_2605_10457_gb300.grca import CAST_BRUTE, CAST_FP64_RECHECK
+    rng = np.random.default_rng(17)
+    n1, n2, n3, n4 = 20, 10, 8, 8
+    parts = [tiny_scene(4, n_tris=200, extent=6.0)]
+    parts.append(np.concatenate([np.zeros((n1, 1, 3)), rng.normal(0.0, 2.0, (n1, 2, 3))], 1))
+    c2 = np.stack([rng.normal(0.0, 0.5, n2), rng.uniform(2.0, 5.0, n2), rng.normal(0.0, 0.5, n2)], -1)[:, None, :]
+    parts.append((c2 + 0.7 * rng.normal(0.0, 1.0, (n2, 3, 3))) * 10.0 ** rng.uniform(-16, -12, (n2, 1, 1)))
+    c3 = np.stack([-rng.uniform(2.0, 5.0, n3), rng.normal(0.0, 0.5, n3), rng.normal(0.0, 0.5, n3)], -1)[:, None, :]
+    parts.append((c3 + 0.7 * rng.normal(0.0, 1.0, (n3, 3, 3))) * 1e-20)
+    c4 = np.stack([rng.uniform(2.0, 5.0, n4), -rng.uniform(2.0, 5.0, n4), rng.normal(0.0, 0.3, n4)], -1)[:, None, :]
+    parts.append((c4 + 0.7 * rng.normal(0.0, 1.0, (n4, 3, 3))) * 10.0 ** rng.uniform(-7, -5, (n4, 1, 1)))
+    tris = np.ascontiguousarray(np.concatenate(parts, 0).astype(np.float32))
+    sens = [make_sensor((0.0, 0.0, 0.0), channels="c32", n_rays=360),
+            make_sensor((0.0, 0.0, 0.0), yaw=0.7, channels="uniform16", n_rays=256, pitch=0.3, roll=-0.2),
+            make_sensor((0.4, -0.3, 0.2), channels="c32", n_rays=360)]
+    c = _caster()
+    ids = [c.add_sensor(s) for s in sens]
+    c.upload(tris)
+    for fl in (0, CAST_FP64_RECHECK):
+        d0, t0 = _cast(c, ids, fl)
+        assert c.stats()["device_error"] == 0
+        d1, t1 = _cast(c, ids, fl | CAST_BRUTE)
+        assert np.array_equal(t0, t1), (fl, np.nonzero(t0 != t1)[0][:8])
+    b = 200 + n1
+    for lo, hi in ((b, b + n2), (b + n2, b + n2 + n3), (b + n2 + n3, b + n2 + n3 + n4)):
+        assert np.isin(t0, np.arange(lo, hi)).sum() > 300   # each kind of small triangle is hit
+    sc = type("S", (), {"sensors": sens})
+    g = _check(sc, tris, d0, t0)
+    assert g["errors"] == 0, g
+
+
 def test_far_from_the_world_origin_brute_equals_culled():
     """Sensors and scene about 3 km from the world origin, where the FP32
     origin's low part o_lo reaches 1e-4 m: the elevation and range culls
