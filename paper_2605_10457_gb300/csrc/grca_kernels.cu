@@ -8,8 +8,8 @@
 //              tiles (GACP-T_g, Sec. 10.1.1) when a range is set, emitter
 //              transform, back-face / range culls (App. A.4.1 Step 1) and the
 //              channel span from the exact elevation extent (replaces the
-//              binary search of Sec. 3.6); survivors go to a queue, sorted by
-//              sensor per warp flush.
+//              binary search of Sec. 3.6); survivors go to a queue, grouped
+//              by sensor within each tile.
 //   k_cull_b   every survivor, warp-cooperative: azimuth span from the vertex
 //              projections (Sec. 3.7), then the pair setup and inline tests of
 //              small spans, or an append to the deferred queue (App. A.4.1 Step 4 and A.5.3, BAT
@@ -1218,61 +1218,28 @@ __global__ void __launch_bounds__(256, 3) k_cull(CastArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int ELEV_GROUP = 8;  // sensors per k_cull_a launch (the sensor loop is unrolled over them)
 constexpr int SURV_BUF = 352;    // per-warp survivor buffer; flushed before a step could overflow it
-constexpr int MAX_SENSORS_SORT = 64;
 struct CullAWarpSmem {
     float tri[32 * 9 + 4];
     unsigned long long buf[SURV_BUF];
-    uint16_t rank[SURV_BUF];            // rank of each entry within its sensor's bucket
-    uint32_t hist[MAX_SENSORS_SORT];    // per-sensor counts, then bucket offsets
 };
 static_assert(sizeof(CullAWarpSmem) % 16 == 0, "per-warp staging must stay 16-byte aligned");
 static_assert(SURV_BUF >= 32 * ELEV_GROUP, "a tile must fit an empty buffer");
 
-// Flush a warp's survivor buffer to the global queue, counting-sorted by
-// sensor so that k_cull_b's batches of 32 mostly hold one sensor (uniform
-// descriptor reads, one azimuth table per batch in L1).
-__device__ __forceinline__ void flush_survivors(const CastArgs& a, CullAWarpSmem& W, uint32_t& fill, uint32_t lane,
-                                                uint32_t n_sensors) {
+// Flush a warp's survivor buffer to the global queue in its order: one
+// atomic for the whole buffer, coalesced 8-byte stores.  The sensor loop
+// appends a tile's survivors sensor by sensor, so a batch of 32 survivors in
+// k_cull_b holds runs of a few sensors.  (A counting sort by sensor here, to
+// give k_cull_b single-sensor batches, cost k_cull_a 15 % and saved k_cull_b
+// nothing.)
+__device__ __forceinline__ void flush_survivors(const CastArgs& a, CullAWarpSmem& W, uint32_t& fill, uint32_t lane) {
     if (fill == 0) return;
-    for (uint32_t s = lane; s < n_sensors; s += 32) W.hist[s] = 0;
-    __syncwarp();
-    for (uint32_t q0 = 0; q0 < fill; q0 += 32) {
-        // one shared atomic per distinct sensor among 32 entries
-        const uint32_t q = q0 + lane;
-        const bool v = q < fill;
-        const uint32_t sn = v ? (uint32_t)(W.buf[q] >> 53) : 0xFFFFu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, sn);
-        const uint32_t leader = __ffs(peers) - 1;
-        uint32_t b = 0;
-        if (v && lane == leader) b = atomicAdd(&W.hist[sn], (uint32_t)__popc(peers));
-        b = __shfl_sync(0xffffffffu, b, leader);
-        if (v) W.rank[q] = (uint16_t)(b + __popc(peers & ((1u << lane) - 1u)));
-    }
-    __syncwarp();
-    // exclusive prefix over the sensor counts (n_sensors <= 64: two per lane)
-    uint32_t h0 = lane < n_sensors ? W.hist[lane] : 0u, h1 = lane + 32 < n_sensors ? W.hist[lane + 32] : 0u;
-    uint32_t i0 = h0, i1 = h1;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t0 = __shfl_up_sync(0xffffffffu, i0, o), t1 = __shfl_up_sync(0xffffffffu, i1, o);
-        if ((int)lane >= o) {
-            i0 += t0;
-            i1 += t1;
-        }
-    }
-    uint32_t tot0 = __shfl_sync(0xffffffffu, i0, 31);
-    __syncwarp();
-    if (lane < n_sensors) W.hist[lane] = i0 - h0;
-    if (lane + 32 < n_sensors) W.hist[lane + 32] = tot0 + i1 - h1;
     uint32_t b0 = 0;
     if (lane == 0) b0 = atomicAdd(&a.qcount[Q_SURV], fill);
     b0 = __shfl_sync(0xffffffffu, b0, 0);
-    __syncwarp();
     for (uint32_t q = lane; q < fill; q += 32) {
-        unsigned long long e = W.buf[q];
-        uint32_t dst = b0 + W.hist[e >> 53] + W.rank[q];
+        const uint32_t dst = b0 + q;
         if (dst < a.surv_cap)
-            a.surv[dst] = e;
+            a.surv[dst] = W.buf[q];
         else
             atomicOr(a.error, (uint32_t)ERR_SURV_CAP);
     }
@@ -1628,7 +1595,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
             }
             if (live == 0) continue;  // the whole tile: no load, no per-triangle work
         }
-        if (fill + 32 * ns > SURV_BUF) flush_survivors(a, W, fill, lane, a.n_sensors);
+        if (fill + 32 * ns > SURV_BUF) flush_survivors(a, W, fill, lane);
         stage_tris(a, base, cnt, W.tri, lane);
         {
             // the warp's next tile into L2 while this one is worked on (9 lines of 128 B)
@@ -1662,7 +1629,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
         }
         __syncwarp();
     }
-    flush_survivors(a, W, fill, lane, a.n_sensors);
+    flush_survivors(a, W, fill, lane);
     if (groups && lane == 0 && g_culled) atomicAdd(&a.counters[C_GROUP], (unsigned long long)g_culled);
 }
 
