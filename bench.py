@@ -703,7 +703,10 @@ def main():
     if dom_name == "k_cull_a":
         flops = pairs * F_CULL_A
     elif dom_name == "k_cull_b":
-        flops = (st_prof["survivors"] * F_CULL_B + st_prof["pairs_live"] * F_SETUP
+        # setups only for the live pairs that get one: not the deferred ones
+        # (set up by k_expand) nor those dropped as occluded
+        setups = st_prof["pairs_live"] - st_prof["big_pairs"] - st_prof.get("pairs_occluded", 0)
+        flops = (st_prof["survivors"] * F_CULL_B + setups * F_SETUP
                  + st_prof["candidates_inline"] * F_TEST)
     elif dom_name == "k_test":
         flops = (st_prof["tests"] - st_prof["candidates_inline"]) * F_TEST
@@ -716,8 +719,9 @@ def main():
                 "frac": achieved / fp32_peak if fp32_peak else None, "traffic": measured_traffic(dom_name, traffic_key),
                 "peak_source": f"FP32 {n_sm} SM x 128 lanes x 2 x {sm_max:.0f} MHz (unit counts and max clock)",
                 "algorithmic": {"k_cull_a": f"{F_CULL_A:.0f} flop per (tri, sensor) pair",
-                                "k_cull_b": f"{F_CULL_B:.0f} flop per surviving pair + {F_SETUP:.0f} per live pair "
-                                            f"(setup) + {F_TEST:.0f} per inline test",
+                                "k_cull_b": f"{F_CULL_B:.0f} flop per surviving pair + {F_SETUP:.0f} per live pair set "
+                                            f"up inline (not deferred, not dropped as occluded) + "
+                                            f"{F_TEST:.0f} per inline test",
                                 "k_test": f"{F_TEST:.0f} flop per queued test"},
                 "avg_launch_ms": avg_ms,
                 "hbm_vertex_stream_gbs": hbm_achieved, "hbm_peak_gbs": peaks.get("hbm_gbs"),
@@ -803,7 +807,8 @@ def main():
                                           "chunks", "tests", "hits", "uncertain", "ties", "flagged_rays",
                                           "recheck_pairs", "group_culled", "bvh_node_visits", "bvh_tests",
                                           "queued_edge", "queued_t", "queued_range", "queued_orient", "queued_tie",
-                                          "kept_edge", "kept_t", "kept_range", "kept_orient", "kept_tie")},
+                                          "kept_edge", "kept_t", "kept_range", "kept_orient", "kept_tie",
+                                          "t_refined", "pairs_occluded")},
         "autotune_ms": tune_ms,
         "launch_config": launch_cfg,
         "static_build_s": build_s,

@@ -97,7 +97,17 @@ enum {
      * unchanged.  The next frame on the context runs meanwhile (only its key
      * decode waits for this copy-out), so a caller that alternates two pairs
      * of host arrays overlaps each frame's copy-out with the next frame. */
-    GRCA_CAST_HOST_ASYNC = 1u << 8
+    GRCA_CAST_HOST_ASYNC = 1u << 8,
+    /* Test every candidate even where its ray already holds a closer hit.
+     * By default an FP32+recheck cast drops, before its test setup, a
+     * (triangle, sensor) pair of at most 4 candidate rays when every one of
+     * those rays already holds a certain hit closer than the pair's distance
+     * lower bound (nearest vertex minus longest edge) by more than the tie
+     * band (counted in grca_stats.pairs_occluded), and drops single
+     * candidates of large pairs the same way in their per-channel test pass.
+     * None of the dropped tests could change the result, so the output is
+     * the same bits either way.  For A/B timing and debugging. */
+    GRCA_CAST_NO_OCCLUSION = 1u << 9
 };
 
 /* Context options (all fields 0 = library default). */
@@ -179,6 +189,12 @@ typedef struct {
      * before the filter; the settled ones are committed as certain hits or
      * dropped as misses and are never kept. */
     uint64_t t_refined;
+    /* live pairs (FP32+recheck casts, at most 8 candidate rays) dropped
+     * before their test setup because every candidate ray already held a
+     * certain hit closer than the pair's distance lower bound (nearest
+     * vertex minus longest edge) by more than the tie band: none of their
+     * tests could change the result.  Counted in pairs_live as well. */
+    uint64_t pairs_occluded;
 } grca_stats;
 
 /* Create a context on CUDA device `device`.  `opt` may be NULL.

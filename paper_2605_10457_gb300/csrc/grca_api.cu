@@ -744,7 +744,7 @@ static void fill_sensor(const grca_ctx* ctx, int id, uint32_t ray_off, SensorDev
 static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, float* out_dist, uint32_t* out_tri,
                                 uint32_t flags, cudaStream_t st, CastArgs& a) {
     if (!ids || n < 1 || n > (uint32_t)MAX_SENSORS || !out_dist || !out_tri) return GRCA_ERR_INVALID_ARG;
-    if (flags & ~0xFFu) return GRCA_ERR_INVALID_ARG;
+    if (flags & ~(0xFFu | (uint32_t)GRCA_CAST_NO_OCCLUSION)) return GRCA_ERR_INVALID_ARG;
     if ((flags & GRCA_CAST_DUMP_CANDIDATES) && !ctx->dump) return GRCA_ERR_INVALID_ARG;
     for (uint32_t k = 0; k < n; ++k)
         if (ids[k] < 0 || ids[k] >= (int32_t)ctx->sensors.size()) return GRCA_ERR_INVALID_ARG;
@@ -875,7 +875,8 @@ static grca_status prepare_cast(grca_ctx* ctx, const int32_t* ids, uint32_t n, f
 // launch configurations are tuned per cast shape: sensors, rays, triangles
 // through the culls, and the flags that change the work (not GRAPH or DUMP)
 static std::tuple<uint32_t, uint32_t, uint32_t, uint32_t> tune_key(const CastArgs& a) {
-    return std::make_tuple(a.n_sensors, a.n_rays_total, a.n_tris - a.tri_first, a.flags & 0xE7u);
+    return std::make_tuple(a.n_sensors, a.n_rays_total, a.n_tris - a.tri_first,
+                           a.flags & (0xE7u | (uint32_t)GRCA_CAST_NO_OCCLUSION));
 }
 
 static LaunchCfg cfg_for(grca_ctx* ctx, const CastArgs& a) {
@@ -1222,6 +1223,7 @@ grca_status grca_get_stats(grca_ctx* ctx, grca_stats* out, void* stream) {
         kp[k] = c[C_KEPT0 + k];
     }
     out->t_refined = c[C_REFINED];
+    out->pairs_occluded = c[C_OCCLUDED];
     return err ? GRCA_ERR_CAPACITY : GRCA_OK;
 }
 
@@ -1257,7 +1259,8 @@ grca_status grca_profile_read(grca_ctx* ctx, uint32_t max, const char** names, u
 grca_status grca_get_launch_config(grca_ctx* ctx, const int32_t* ids, uint32_t n, uint32_t flags,
                                   int32_t out[4]) {
     if (!ctx || !out) return GRCA_ERR_INVALID_ARG;
-    if (!ids || n < 1 || n > (uint32_t)MAX_SENSORS || (flags & ~0xFFu)) return GRCA_ERR_INVALID_ARG;
+    if (!ids || n < 1 || n > (uint32_t)MAX_SENSORS || (flags & ~(0xFFu | (uint32_t)GRCA_CAST_NO_OCCLUSION)))
+        return GRCA_ERR_INVALID_ARG;
     uint32_t rays = 0;
     for (uint32_t k = 0; k < n; ++k) {
         if (ids[k] < 0 || ids[k] >= (int32_t)ctx->sensors.size()) return GRCA_ERR_INVALID_ARG;

@@ -36,6 +36,7 @@ enum {
     C_QUEUED0 = 16,   // re-test queue entries per cause (UC_*), C_QUEUED0 + cause
     C_KEPT0 = 21,     // entries per cause kept by the filter (their rays are flagged)
     C_REFINED = 26,   // entries of cause UC_T whose t was re-evaluated in double-float
+    C_OCCLUDED = 27,  // live pairs dropped before their setup: every candidate ray already holds a closer hit
     C_NUM = 32
 };
 // why a (ray, triangle) pair went to the FP64 re-test queue
@@ -102,7 +103,7 @@ inline void build_channel_lut(const float* sins, uint32_t n, float& lo_out, floa
 }
 
 // Per (triangle, sensor) test setup: everything the per-candidate
-// ray-triangle test needs (emitter frame), 80 bytes.
+// ray-triangle test needs (emitter frame), 88 bytes (96 with alignment).
 struct __align__(16) PairSetup {
     float m[9];      // folded edge-plane normals: forward hit <=> all d.m_k >= 0
     float tau[3];    // per-edge FP32 error bound of d.m_k
@@ -111,7 +112,7 @@ struct __align__(16) PairSetup {
     float err_det;   // relative FP32 error bound of det
     uint32_t state;  // bit0: |det| within its error bound (facing / orientation uncertain)
     float G[3];      // err(d.n) <= sum_i |d_i| G_i
-    float pad_;
+    float t_lb;      // lower bound of the distance from the origin to any point of the triangle
 };
 
 // A (triangle, sensor) pair deferred to the per-channel span pass (32 bytes).

@@ -135,7 +135,7 @@ __device__ __forceinline__ V3 rel_origin(const SensorDev& S, V3 v) {
 // ---------------------------------------------------------------------------
 // Setup outputs go through a writer: set(k, value) with the field index of
 // the setup views below (m 0-8, tau 9-11, n 12-14, det 15, err_det 16,
-// state 17, G 18-20).
+// state 17, G 18-20, t_lb 21).
 struct SetupWriterAoS {
     PairSetup& s;
     __device__ __forceinline__ void set(int k, float v) { reinterpret_cast<float*>(&s)[k] = v; }
@@ -185,9 +185,27 @@ __device__ __forceinline__ float rcp_up(float x) {
     return __fmul_rn(r, 1.000002f);
 }
 
+// Lower bound of the distance from the sensor origin to every point of the
+// triangle: each point lies within the longest edge of every vertex, so
+// |x - o| >= min_k |p_k| - max_k |p_k1 - p_k|, with p the emitter-frame
+// vertices.  Each p_k is within about 7u |p_k| of the exact rotated
+// difference (origin split, the FP32 rotation of an orthonormal basis, the
+// products), so the edges are within 14u of the farthest vertex's distance;
+// the relative padding of 4e-6 covers that, the rounded squares and the
+// 2^-22 error of the approximate roots.  Explicitly rounded, so every kernel
+// gets the same bits; 0 where the bound is not positive or not finite.
+__device__ __forceinline__ float pair_t_lb(const V3 p[3]) {
+    const float r2min = fminf(vdot(p[0], p[0]), fminf(vdot(p[1], p[1]), vdot(p[2], p[2])));
+    const V3 e0 = vsub(p[1], p[0]), e1 = vsub(p[2], p[1]), e2 = vsub(p[0], p[2]);
+    const float ee = fmaxf(vdot(e0, e0), fmaxf(vdot(e1, e1), vdot(e2, e2)));
+    const float lb = __fsub_rn(__fmul_rn(sqrt_ftz(r2min), 1.f - 4e-6f), __fmul_rn(sqrt_ftz(ee), 1.f + 4e-6f));
+    return lb > 0.f ? lb : 0.f;
+}
+
 template <typename WR>
 __device__ __forceinline__ void make_setup(const SensorDev& S, const TriW& T, const V3 w[3], const V3 p[3], float det,
                                            float err_det_abs, WR out) {
+    out.set(21, pair_t_lb(p));
     bool unc = fabsf(det) <= err_det_abs;
     // forward hit <=> every emitter-frame edge function has the sign of the
     // emitter-frame triple product p0.(p1 x p2) = det(B) * det
@@ -264,11 +282,12 @@ __device__ __forceinline__ V3 ray_dir(float2 ch, float2 az) {
 // guaranteed; *t_err receives the relative error bound of t.
 // A pair setup is read through a view: the PairSetup struct itself, or one
 // lane's column of a field-major shared-memory copy (conflict-free).
-// Field index: m 0-8, tau 9-11, n 12-14, det 15, err_det 16, state 17, G 18-20.
-constexpr int SETUP_FIELDS = 21;
+// Field index: m 0-8, tau 9-11, n 12-14, det 15, err_det 16, state 17, G 18-20,
+// distance lower bound 21.
+constexpr int SETUP_FIELDS = 22;
 static_assert(offsetof(PairSetup, tau) == 9 * 4 && offsetof(PairSetup, n) == 12 * 4 && offsetof(PairSetup, det) == 15 * 4 &&
                   offsetof(PairSetup, err_det) == 16 * 4 && offsetof(PairSetup, state) == 17 * 4 &&
-                  offsetof(PairSetup, G) == 18 * 4,
+                  offsetof(PairSetup, G) == 18 * 4 && offsetof(PairSetup, t_lb) == 21 * 4,
               "setup field indices");
 struct SetupAoS {
     const PairSetup& s;
@@ -357,6 +376,21 @@ __device__ __forceinline__ void push_recheck(const CastArgs& a, uint32_t g, uint
         a.recheck[idx] = make_uint4(g, tri, __float_as_uint(t_lo), cause);
     else
         atomicOr(a.error, (uint32_t)ERR_RECHECK_CAP);
+}
+
+// An uncertain FP32 result goes to the re-test queue with a lower bound of
+// its distance: t (1 - t_err) where that error bound is usable, raised to the
+// pair's distance lower bound t_lb (0 where none is known).  It is not queued
+// when that bound lies beyond the tie band of the ray's current best hit: the
+// filter would drop it against the final winner, which is no farther.
+// Returns 1 if queued.
+__device__ __forceinline__ uint32_t queue_uncertain(const CastArgs& a, uint32_t g, uint32_t tri, int res, float t,
+                                                    float t_err, float t_lb, float tcur) {
+    const bool t_ok = t_err < 0.25f && t > 0.f;
+    const float t_lo = t_ok ? fmaxf(__fmul_rn(t, __fsub_rn(1.f, t_err)), t_lb) : t_lb;
+    if (t_lo > __fmul_rn(tcur, 1.f + BETA)) return 0u;
+    push_recheck(a, g, tri, t_lo, (uint32_t)(res - T_UNCERTAIN));
+    return 1u;
 }
 
 __device__ __noinline__ void dump_candidate(const CastArgs& a, uint32_t g, uint32_t tri) {
@@ -476,17 +510,13 @@ __device__ __noinline__ Refined refine_t(const CastArgs& a, const SensorDev& S, 
 // Returns 1 if a hit was committed (for the statistics).
 template <bool RECHECK>
 __device__ __forceinline__ int commit_pre(const CastArgs& a, uint32_t g, uint32_t tri, int res, float t, float t_err,
-                                          unsigned long long cur, uint32_t& n_unc, uint32_t& n_ties) {
+                                          float t_lb, unsigned long long cur, uint32_t& n_unc, uint32_t& n_ties) {
     if (res == T_MISS) return 0;
     unsigned long long* kp = &a.keys[g];
     float tcur = __uint_as_float((uint32_t)(cur >> 32));
     if (is_uncertain(res)) {
         // a re-test can only change the result if it may beat the current best
-        const bool t_ok = t_err < 0.25f && t > 0.f;
-        const float t_lo = __fmul_rn(t, __fsub_rn(1.f, t_err));
-        if (t_ok && t_lo > __fmul_rn(tcur, 1.f + BETA)) return 0;
-        push_recheck(a, g, tri, t_ok ? t_lo : 0.f, (uint32_t)(res - T_UNCERTAIN));
-        n_unc++;
+        n_unc += queue_uncertain(a, g, tri, res, t, t_err, t_lb, tcur);
         return 0;
     }
     unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | tri;
@@ -510,9 +540,9 @@ __device__ __forceinline__ int commit_pre(const CastArgs& a, uint32_t g, uint32_
 
 template <bool RECHECK>
 __device__ __forceinline__ int commit(const CastArgs& a, uint32_t g, uint32_t tri, int res, float t, float t_err,
-                                      uint32_t& n_unc, uint32_t& n_ties) {
+                                      float t_lb, uint32_t& n_unc, uint32_t& n_ties) {
     if (res == T_MISS) return 0;
-    return commit_pre<RECHECK>(a, g, tri, res, t, t_err, __ldcg(&a.keys[g]), n_unc, n_ties);
+    return commit_pre<RECHECK>(a, g, tri, res, t, t_err, t_lb, __ldcg(&a.keys[g]), n_unc, n_ties);
 }
 
 // ---------------------------------------------------------------------------
@@ -1070,7 +1100,7 @@ __device__ __forceinline__ void cull_rest(const CastArgs& a, const SensorDev& S,
             int res = test_fp32<RECHECK>(SetupAoS{st}, S, d, t, terr);
             c.tests++;
             if (dump) dump_candidate(a, gbase + i, tri);
-            c.hits += commit<RECHECK>(a, gbase + i, tri, res, t, terr, c.unc, c.ties);
+            c.hits += commit<RECHECK>(a, gbase + i, tri, res, t, terr, st.t_lb, c.unc, c.ties);
             if (++i == n) i = 0;
         }
     }
@@ -1651,7 +1681,7 @@ struct CullBWarpSmem {
     float inv[32];               // per pair: rounded-up 1 / ray count
     uint32_t own[32];            // lane of the pair with the r-th candidate run (r-th set bit of the owner mask)
     uint4 pend[64];              // live pairs waiting for their setup: triangle, meta, first ray, candidates
-    uint32_t cnt[8];             // live, cand, inl, big, tests, hits, unc, ties
+    uint32_t cnt[9];             // live, cand, inl, big, tests, hits, unc, ties, occluded
 };
 
 // Tie check of a committed certain hit against the key its atomicMin
@@ -1726,12 +1756,7 @@ __device__ __forceinline__ void cull_b_test_pairs(const CastArgs& a, const CullS
             if (res != T_MISS) {
                 const float tcur = __uint_as_float((uint32_t)(cur >> 32));
                 if (is_uncertain(res)) {
-                    const bool t_ok = terr < 0.25f && t > 0.f;
-                    const float t_lo = __fmul_rn(t, __fsub_rn(1.f, terr));
-                    if (!(t_ok && t_lo > __fmul_rn(tcur, 1.f + BETA))) {
-                        push_recheck(a, g, tri, t_ok ? t_lo : 0.f, (uint32_t)(res - T_UNCERTAIN));
-                        c_unc++;
-                    }
+                    c_unc += queue_uncertain(a, g, tri, res, t, terr, W.st[21][lane], tcur);
                 } else {
                     c_hits++;
                     const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | tri;
@@ -1820,12 +1845,7 @@ __device__ __forceinline__ void cull_b_test_pairs(const CastArgs& a, const CullS
         const float tcur = __uint_as_float((uint32_t)(cur >> 32));
         if (is_uncertain(res)) {
             // a re-test can only change the result if it may beat the current best
-            const bool t_ok = terr < 0.25f && t > 0.f;
-            const float t_lo = __fmul_rn(t, __fsub_rn(1.f, terr));
-            if (!(t_ok && t_lo > __fmul_rn(tcur, 1.f + BETA))) {
-                push_recheck(a, g, tri, t_ok ? t_lo : 0.f, (uint32_t)(res - T_UNCERTAIN));
-                c_unc++;
-            }
+            c_unc += queue_uncertain(a, g, tri, res, t, terr, W.st[21][own & 31u], tcur);
             continue;
         }
         c_hits++;
@@ -1844,6 +1864,47 @@ __device__ __forceinline__ void cull_b_test_pairs(const CastArgs& a, const CullS
     __syncwarp();
 }
 
+// A live pair with at most OCC_MAX candidate rays is dropped before its
+// setup when every candidate ray already holds a certain hit (the keys hold
+// only those) whose FP32 distance, widened by the tie band, lies below the
+// pair's distance lower bound less the FP32 error of a certain t.  None of
+// its candidates could then win, tie or be kept for the re-test: a certain
+// hit of the pair would be farther than tcur (1 + BETA) and is never
+// committed, and an uncertain one has a lower bound of at least t_lb, which
+// queue_uncertain does not queue.  Keys only decrease, so the test loop
+// would drop every candidate of the pair as well, and the result is the same
+// bits.  The candidate keys are read (high words, L2) before they are compared.
+// Casts that dump their candidates (a debug mode that checks the culls'
+// superset) or pass GRCA_CAST_NO_OCCLUSION drop no pair this way.
+constexpr uint32_t OCC_MAX = 4;
+__device__ __forceinline__ bool pair_occluded(const CastArgs& a, const SensorDev& S, const V3 p[3], uint32_t j0,
+                                              uint32_t r0, uint32_t n_r, uint32_t nc) {
+    const float lb = pair_t_lb(p);
+    if (!(lb > 0.f)) return false;
+    const float thr = __fmul_rn(lb, 1.f - 2.f * TAU_T);
+    const unsigned int* hw = reinterpret_cast<const unsigned int*>(a.keys) + 1;   // t bits of key g at 2g + 1
+    float tk[OCC_MAX];
+    uint32_t j = j0, i = r0, io = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < OCC_MAX; ++q) {
+        tk[q] = 0.f;
+        if (q < nc) {
+            tk[q] = __uint_as_float(__ldcg(hw + 2ull * (S.ray_off + j * S.n_rays + i)));
+            if (++i == S.n_rays) i = 0;
+            if (++io == n_r) {
+                io = 0;
+                ++j;
+                i = r0;
+            }
+        }
+    }
+    bool occ = true;
+#pragma unroll
+    for (uint32_t q = 0; q < OCC_MAX; ++q)
+        if (q < nc) occ = occ && thr > __fmul_rn(tk[q], 1.f + BETA);
+    return occ;
+}
+
 template <bool RECHECK, bool BRUTE>
 __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1851,7 +1912,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
     const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
     CullBWarpSmem& W = reinterpret_cast<CullBWarpSmem*>(M.rest)[wib];
     const bool dump = a.flags & 16u;
-    if (lane < 8) W.cnt[lane] = 0;
+    if (lane < 9) W.cnt[lane] = 0;
     __syncwarp();
     uint32_t c_unc = 0, c_ties = 0, c_hits = 0;
     const uint32_t n = min(*(volatile uint32_t*)&a.qcount[Q_SURV], a.surv_cap);
@@ -1867,7 +1928,7 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
     uint32_t fill = 0;
     for (uint32_t b0 = s0 + gwarp * 32; b0 < n; b0 += n_warps * 32) {
         const uint32_t q = b0 + lane;
-        uint32_t l_live = 0, l_cand = 0, l_big = 0;
+        uint32_t l_live = 0, l_cand = 0, l_big = 0, l_occ = 0;
         bool pend_me = false;
         uint4 pe = make_uint4(0u, 0u, 0u, 0u);
         if (q < n) {
@@ -1953,9 +2014,15 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
                     }
                     l_big = 1;
                 } else {
-                    pend_me = true;
-                    pe = make_uint4(tri, (uint32_t)sp.j_lo | ((uint32_t)sp.n_r << 10) | (sn << 26),
-                                    (uint32_t)imod(sp.u_lo, (int)S.n_rays), nc);
+                    const uint32_t r0 = (uint32_t)imod(sp.u_lo, (int)S.n_rays);
+                    if (RECHECK && !BRUTE && !dump && !(a.flags & (uint32_t)GRCA_CAST_NO_OCCLUSION) &&
+                        nc <= OCC_MAX &&
+                        pair_occluded(a, S, p, (uint32_t)sp.j_lo, r0, (uint32_t)sp.n_r, nc)) {
+                        l_occ = 1;
+                    } else {
+                        pend_me = true;
+                        pe = make_uint4(tri, (uint32_t)sp.j_lo | ((uint32_t)sp.n_r << 10) | (sn << 26), r0, nc);
+                    }
                 }
             }
         }
@@ -1964,11 +2031,12 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
         fill += __popc(bal);
         {
             const uint32_t s_live = __reduce_add_sync(0xffffffffu, l_live), s_cand = __reduce_add_sync(0xffffffffu, l_cand),
-                           s_big = __reduce_add_sync(0xffffffffu, l_big);
+                           s_big = __reduce_add_sync(0xffffffffu, l_big), s_occ = __reduce_add_sync(0xffffffffu, l_occ);
             if (lane == 0) {
                 W.cnt[0] += s_live;
                 W.cnt[1] += s_cand;
                 W.cnt[3] += s_big;
+                W.cnt[8] += s_occ;
             }
         }
         __syncwarp();
@@ -1985,12 +2053,12 @@ __global__ void __launch_bounds__(256, 4) k_cull_b(CastArgs a) {
     c_hits = __reduce_add_sync(0xffffffffu, c_hits);
     __syncwarp();
     if (lane == 0) {
-        const int idx[8] = {C_PAIRS_LIVE, C_CAND, C_CAND_INLINE, C_BIG, C_TESTS, C_HITS, C_UNCERTAIN, C_TIES};
+        const int idx[9] = {C_PAIRS_LIVE, C_CAND, C_CAND_INLINE, C_BIG, C_TESTS, C_HITS, C_UNCERTAIN, C_TIES, C_OCCLUDED};
         W.cnt[5] += c_hits;
         W.cnt[6] = c_unc;
         W.cnt[7] = c_ties;
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < 9; ++k)
             if (W.cnt[k]) atomicAdd(&a.counters[idx[k]], (unsigned long long)W.cnt[k]);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[C_SURV] = *(volatile uint32_t*)&a.qcount[Q_SURV];
@@ -2183,6 +2251,7 @@ __global__ void __launch_bounds__(256, 4) k_test(CastArgs a) {
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t n_chunks = min(*(volatile uint32_t*)&a.qcount[Q_CHUNK], a.chunk_cap);
     const bool dump = a.flags & 16u;
+    const bool occl = RECHECK && !dump && !(a.flags & (uint32_t)GRCA_CAST_NO_OCCLUSION);
     uint32_t c_tests = 0, c_hits = 0, c_unc = 0, c_ties = 0;
     for (uint32_t c = gw; c < n_chunks; c += nw) {
         uint4 ck = a.chunks[c];
@@ -2196,12 +2265,19 @@ __global__ void __launch_bounds__(256, 4) k_test(CastArgs a) {
         for (uint32_t q = lane; q < cnt; q += 32) {
             uint32_t i = r0 + q;
             if (i >= n) i -= n;
+            // a candidate whose ray already holds a certain hit closer than the
+            // pair's distance lower bound by more than the tie band is dropped,
+            // as in k_cull_b (the same bits)
+            const unsigned long long cur = __ldcg(&a.keys[gbase + i]);
+            if (occl && __fmul_rn(st.t_lb, 1.f - 2.f * TAU_T) >
+                            __fmul_rn(__uint_as_float((uint32_t)(cur >> 32)), 1.f + BETA))
+                continue;
             V3 d = ray_dir(chv, __ldg(&a.az_sc[S.az_off + i]));
             float t, terr;
             int res = test_fp32<RECHECK>(SetupAoS{st}, S, d, t, terr);
             c_tests++;
             if (dump) dump_candidate(a, gbase + i, tri);
-            c_hits += commit<RECHECK>(a, gbase + i, tri, res, t, terr, c_unc, c_ties);
+            c_hits += commit_pre<RECHECK>(a, gbase + i, tri, res, t, terr, st.t_lb, cur, c_unc, c_ties);
         }
     }
     warp_add(&a.counters[C_TESTS], c_tests);
@@ -2671,7 +2747,7 @@ __global__ void __launch_bounds__(BVH_BLOCK, 4) k_bvh(CastArgs a) {
                 const int res = test_fp32<RECHECK>(sr, S, d, t, terr);
                 if (res == T_MISS) continue;
                 const uint32_t tri = __ldg(a.bvh_prim + k);
-                commit_pre<RECHECK>(a, g, tri, res, t, terr, cur, c_unc, c_ties);
+                commit_pre<RECHECK>(a, g, tri, res, t, terr, sr.f(21), cur, c_unc, c_ties);
                 if (res == T_HIT) {
                     const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | tri;
                     if (key < cur) cur = key;

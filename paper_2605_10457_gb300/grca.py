@@ -26,6 +26,7 @@ CAST_LOSSY_AREA = 1 << 5
 CAST_NO_GROUP_CULL = 1 << 6
 CAST_NO_STATIC_BVH = 1 << 7
 CAST_HOST_ASYNC = 1 << 8
+CAST_NO_OCCLUSION = 1 << 9
 NO_HIT = 0xFFFFFFFF
 
 
@@ -52,7 +53,8 @@ class grca_stats(ctypes.Structure):
                                                "n_rays")] + \
                [("device_error", ctypes.c_uint32), ("reserved", ctypes.c_uint32)] + \
                [(f"{w}_{c}", ctypes.c_uint64) for w in ("queued", "kept")
-                for c in ("edge", "t", "range", "orient", "tie")] + [("t_refined", ctypes.c_uint64)]
+                for c in ("edge", "t", "range", "orient", "tie")] + \
+               [("t_refined", ctypes.c_uint64), ("pairs_occluded", ctypes.c_uint64)]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}

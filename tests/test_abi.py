@@ -83,7 +83,7 @@ def test_struct_layouts_match_header():
     # the ctypes mirrors must match the C layout (sizes computed by the C rules)
     assert ctypes.sizeof(grca.grca_sensor_desc) == 12 * 8 + 8 + 4 + 4 + 4 * 8
     assert ctypes.sizeof(grca.grca_options) == 3 * 8 + 4 * 4 + 8 + 8
-    assert ctypes.sizeof(grca.grca_stats) == 17 * 8 + 2 * 4 + 11 * 8
+    assert ctypes.sizeof(grca.grca_stats) == 17 * 8 + 2 * 4 + 12 * 8
 
 
 def test_build_targets_sm103a_only():

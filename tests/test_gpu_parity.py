@@ -109,6 +109,35 @@ def test_launch_configuration_does_not_change_the_result(cfg):
             assert np.array_equal(d.view(np.uint32), ref[0].view(np.uint32)), (k, fl)
 
 
+@pytest.mark.parametrize("cfg", ["c4m", "c5m"])
+def test_occlusion_drop_does_not_change_the_result(cfg):
+    """An FP32 + re-test cast drops a live pair of at most 4 candidate rays
+    before its setup when each of those rays already holds a certain hit
+    closer than the pair's distance lower bound by more than the tie band.
+    Such a pair could neither win, tie nor be kept for the re-test, so the
+    output equals the cast that tests every pair (GRCA_CAST_NO_OCCLUSION),
+    bit for bit, over several animated frames and two launch configurations."""
+    from paper_2605_10457_gb300.grca import CAST_FP64_RECHECK, CAST_GRAPH, CAST_NO_OCCLUSION
+    sc = make_config(cfg)
+    for k in (dict(), dict(inline_max=1024, chunk_rays=256, cull_block=256, cull_blocks_per_sm=16)):
+        c, ids, tris = _setup(sc, big_pair_capacity=1 << 20, chunk_capacity=16 << 20, **k)
+        for frame in (0, 7):
+            c.update(sc.tris(frame), 0)
+            d0, t0 = _cast(c, ids, CAST_FP64_RECHECK | CAST_GRAPH)
+            st0 = c.stats()
+            d1, t1 = _cast(c, ids, CAST_FP64_RECHECK | CAST_GRAPH | CAST_NO_OCCLUSION)
+            st1 = c.stats()
+            assert st0["pairs_occluded"] > 0 and st1["pairs_occluded"] == 0, (st0, st1)
+            assert st0["pairs_live"] == st1["pairs_live"] and st0["tests"] < st1["tests"]
+            assert np.array_equal(t0, t1), (cfg, k, frame, np.nonzero(t0 != t1)[0][:8])
+            assert np.array_equal(d0.view(np.uint32), d1.view(np.uint32)), (cfg, k, frame)
+            assert st0["flagged_rays"] == st1["flagged_rays"]
+        # the plain FP32 path drops nothing this way
+        _cast(c, ids, 0)
+        assert c.stats()["pairs_occluded"] == 0
+        c.close()
+
+
 def test_tiny_random_scenes_brute_equals_culled():
     from paper_2605_10457_gb300.grca import CAST_BRUTE, CAST_FP64_RECHECK
     for seed in range(6):
