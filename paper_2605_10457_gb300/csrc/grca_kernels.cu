@@ -1666,12 +1666,13 @@ __global__ void __launch_bounds__(256, 4) k_cull_a(CastArgs a) {
 // ---------------------------------------------------------------------------
 // k_cull_b: phase B over the survivor queue, warp-cooperative.  Each warp
 // takes 32 survivors at a time: (1) per lane, range cull and azimuth span;
-// large spans go to the deferred queue, small live spans to the warp's list
-// of pending pairs; (2) once 32 pairs are pending, one per lane gets its test
-// setup into shared memory and its first candidate tested; (3) the warp
-// expands all other candidates of those 32 pairs together, one candidate per
-// lane (owner found from the warp's prefix sums), so the setups and tests run
-// with full warps and without lane divergence.
+// large spans go to the deferred queue, small live spans whose candidate rays
+// already hold closer hits are dropped (pair_occluded), the others go to the
+// warp's list of pending pairs; (2) once 32 pairs are pending, one per lane
+// gets its test setup into shared memory; (3) the warp expands and tests all
+// candidates of those 32 pairs together, one candidate per lane (owner found
+// from the warp's prefix sums), so the setups and tests run with full warps
+// and without lane divergence.
 // ---------------------------------------------------------------------------
 struct CullBWarpSmem {
     float st[SETUP_FIELDS][32];  // field-major setups of the warp's 32 pairs
@@ -1700,19 +1701,20 @@ __device__ __forceinline__ void tie_check(const CastArgs& a, uint32_t g, uint32_
     }
 }
 
-// Setup, first test and cooperative candidate expansion of the warp's
-// pending live pairs W.pend[0, np), np <= 32: one pair per lane gets its
-// test setup into shared memory and tests its first candidate, then the warp
-// expands all other candidates of the np pairs together, one candidate per
-// lane per round (owner found from the warp's prefix sums).  The tie check of
-// a commit waits for the next round, so that the atomicMin's returned key
+// Setup and cooperative candidate expansion of the warp's pending live pairs
+// W.pend[0, np), np <= 32: one pair per lane gets its test setup into shared
+// memory, then the warp tests all candidates of the np pairs together, one
+// candidate per lane per round (owner found from the warp's prefix sums).
+// (Testing each pair's first candidate by its setup lane measured 1 % slower
+// on c5: a second inlined copy of the test and commit.)  The tie check of a
+// commit waits for the next round, so that the atomicMin's returned key
 // arrives while that round is tested.  Called by the whole warp.
 template <bool RECHECK>
 __device__ __forceinline__ void cull_b_test_pairs(const CastArgs& a, const CullSmem& M, CullBWarpSmem& W, uint32_t np,
                                                   uint32_t lane, bool dump, uint32_t& c_hits, uint32_t& c_unc,
                                                   uint32_t& c_ties) {
-    uint32_t ncand = 0, tested0 = 0;
-    // a committed hit waiting for its tie check (first the setup lane's own test)
+    uint32_t ncand = 0;
+    // a committed hit waiting for its tie check
     bool pend = false;
     uint32_t pg = 0, ptri = 0;
     float pt = 0.f;
@@ -1743,34 +1745,7 @@ __device__ __forceinline__ void cull_b_test_pairs(const CastArgs& a, const CullS
             W.meta[lane] = meta;
             W.r0[lane] = my_r0;
             W.inv[lane] = __frcp_ru((float)((meta >> 10) & 0xFFFFu));
-            // the pair's first candidate is tested here by its own lane
-            const uint32_t j_lo = meta & 1023u;
-            const uint32_t g = S.ray_off + j_lo * S.n_rays + my_r0;
-            const unsigned long long cur = __ldcg(&a.keys[g]);
-            V3 d = ray_dir(M.ch[S.ch_loc + j_lo], __ldg(&a.az_sc[S.az_off + my_r0]));
-            float t, terr;
-            const int res = test_fp32<RECHECK>(SetupSoA{&W.st[0][0], lane}, S, d, t, terr);
-            if (dump) dump_candidate(a, g, tri);
-            tested0 = 1;
-            ncand = nc - 1;
-            if (res != T_MISS) {
-                const float tcur = __uint_as_float((uint32_t)(cur >> 32));
-                if (is_uncertain(res)) {
-                    c_unc += queue_uncertain(a, g, tri, res, t, terr, W.st[21][lane], tcur);
-                } else {
-                    c_hits++;
-                    const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | tri;
-                    if (!RECHECK) {
-                        if (key < cur) atomicMin(&a.keys[g], key);
-                    } else if (!(t > __fmul_rn(tcur, 1.f + BETA))) {
-                        pold = atomicMin(&a.keys[g], key);
-                        pend = true;
-                        pg = g;
-                        ptri = tri;
-                        pt = t;
-                    }
-                }
-            }
+            ncand = nc;
         }
     }
     // warp prefix sum of the candidate counts
@@ -1784,12 +1759,9 @@ __device__ __forceinline__ void cull_b_test_pairs(const CastArgs& a, const CullS
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
     const uint32_t nz = __ballot_sync(0xffffffffu, ncand > 0);   // lanes that own candidates, in order
     if (ncand > 0) W.own[__popc(nz & ((1u << lane) - 1u))] = lane;
-    {
-        const uint32_t s_t0 = __reduce_add_sync(0xffffffffu, tested0);
-        if (lane == 0) {
-            W.cnt[2] += total + s_t0;
-            W.cnt[4] += total + s_t0;
-        }
+    if (lane == 0) {
+        W.cnt[2] += total;
+        W.cnt[4] += total;
     }
     __syncwarp();
     for (uint32_t c0 = 0; c0 < total; c0 += 32) {
@@ -1813,7 +1785,7 @@ __device__ __forceinline__ void cull_b_test_pairs(const CastArgs& a, const CullS
         if (cc < total) {
             const uint32_t nr = (meta >> 10) & 0xFFFFu;
             const uint32_t sn = meta >> 26;
-            const uint32_t idx = cc - o_excl + 1;   // candidate 0 was tested by the owner lane
+            const uint32_t idx = cc - o_excl;
             // quotient from the rounded-up reciprocal, then one correction
             // step in each direction (enough for idx < 2^24, where (float)idx
             // is exact); a quotient still off (larger spans of the no-cull
