@@ -189,7 +189,7 @@ typedef struct {
      * before the filter; the settled ones are committed as certain hits or
      * dropped as misses and are never kept. */
     uint64_t t_refined;
-    /* live pairs (FP32+recheck casts, at most 8 candidate rays) dropped
+    /* live pairs (FP32+recheck casts, at most 4 candidate rays) dropped
      * before their test setup because every candidate ray already held a
      * certain hit closer than the pair's distance lower bound (nearest
      * vertex minus longest edge) by more than the tie band: none of their

@@ -1295,9 +1295,11 @@ grca_status grca_autotune(grca_ctx* ctx, const int32_t* ids, uint32_t n, float* 
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    // one warm-up cast, then the median of 5 timed casts: the minimum of a
+    // few casts favoured configurations with one lucky run
     auto time_cfg = [&](const LaunchCfg& c, float& ms) -> grca_status {
-        float best = 1e30f;
-        for (int rep = 0; rep < 4; ++rep) {
+        float ts[5];
+        for (int rep = 0; rep < 6; ++rep) {
             CastArgs b = a;
             CK(cudaEventRecord(e0, st));
             grca_status r = run_frame(ctx, b, c, st, false);
@@ -1309,9 +1311,10 @@ grca_status grca_autotune(grca_ctx* ctx, const int32_t* ids, uint32_t n, float* 
             float t;
             CK(cudaEventElapsedTime(&t, e0, e1));
             if (err) t = 1e30f;  // a configuration that overflows a queue is not eligible
-            if (rep > 0) best = std::min(best, t);
+            if (rep > 0) ts[rep - 1] = t;
         }
-        ms = best;
+        std::sort(ts, ts + 5);
+        ms = ts[2];
         return GRCA_OK;
     };
     LaunchCfg best = cfg_for(ctx, a);
