@@ -159,8 +159,8 @@ typedef struct {
     uint64_t candidates_inline; /* of which tested inline by the culling pass */
     uint64_t big_pairs;       /* pairs deferred to the per-channel span pass */
     uint64_t chunks;          /* test chunks emitted by that pass */
-    uint64_t tests;           /* ray-triangle tests run */
-    uint64_t hits;            /* FP32 hits committed to the closest-hit keys */
+    uint64_t tests;           /* ray-triangle tests run (candidates dropped as occluded are not tested) */
+    uint64_t hits;            /* certain FP32 hits those tests found */
     uint64_t uncertain;       /* FP32 tests sent to the FP64 re-test */
     uint64_t ties;            /* tie events between FP32 hits on one ray */
     uint64_t flagged_rays;    /* rays resolved by the FP64 re-test */
