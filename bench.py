@@ -414,6 +414,8 @@ def main():
                     help="device work-queue capacities (small: ~2 GB, for profiler captures)")
     ap.add_argument("--lean", action="store_true", help="headline leg only (no plain / profile / e2e legs)")
     ap.add_argument("--no-group-cull", action="store_true", help="A/B: turn off the group-level (GACP-T_g) cull")
+    ap.add_argument("--no-occlusion", action="store_true",
+                    help="A/B: test every live pair, also those whose candidate rays already hold closer hits")
     ap.add_argument("--no-hybrid-leg", action="store_true", help="skip the hybrid leg reported beside the headline")
     ap.add_argument("--no-lossy-leg", action="store_true", help="skip the lossy apparent-area leg")
     ap.add_argument("--no-variants-leg", action="store_true", help="skip the sensor-variants leg")
@@ -480,7 +482,8 @@ def main():
     n_rays = sc.n_rays
     out = c.outputs(ids)
     stream = torch.cuda.current_stream()
-    FL = grca.CAST_FP64_RECHECK | (grca.CAST_NO_GROUP_CULL if args.no_group_cull else 0)
+    FL = (grca.CAST_FP64_RECHECK | (grca.CAST_NO_GROUP_CULL if args.no_group_cull else 0)
+          | (grca.CAST_NO_OCCLUSION if args.no_occlusion else 0))
 
     tune_ms = None
     if not args.no_autotune:
