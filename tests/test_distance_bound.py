@@ -118,8 +118,8 @@ def test_bound_holds_at_grazing_and_degenerate_shapes():
 def test_bound_holds_for_large_triangles_facing_the_sensor():
     # an equilateral triangle of side L centred on the foot of the perpendicular
     # at distance D: its nearest vertex is about 0.58 L away, its plane only D;
-    # a bound that took less than the whole longest edge off the nearest
-    # vertex would exceed D once L is large against D
+    # a bound that took less than L / sqrt(3) off the nearest vertex would
+    # exceed D once L is large against D
     rng = np.random.default_rng(3)
     for _ in range(500):
         D = 10 ** rng.uniform(-1, 1.5)
